@@ -1,0 +1,483 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form printed in the paper, an exact invariant of the method, a textbook
+special case, number-theoretic lattice-point counts, or a different
+algorithm (FFT convolution) for the same sum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1105_3634_gb300 import workloads as W
+
+CS2 = 1.0 / 3.0
+
+
+# ------------------------------------------------------------ velocity set
+def test_d3q19_isotropy(orc):
+    """Weights and velocities reproduce the Maxwellian moments up to fourth
+    order: sum w = 1, sum w c = 0, sum w cc = cs2 I, sum w cccc = cs4 (dd+dd+dd)."""
+    c, w = orc.velocities()
+    c = c.astype(float)
+    assert len(w) == 19
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(np.einsum("i,ia->a", w, c)).max() < 1e-15
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), CS2 * np.eye(3), atol=1e-15)
+    d = np.eye(3)
+    iso = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso, atol=1e-15)
+    # every velocity has its opposite
+    s = {tuple(v) for v in c.astype(int)}
+    assert all(tuple(-np.array(v)) in s for v in s)
+
+
+# ------------------------------------------------------------ stencil sets
+def _r3(kmax):
+    """Number of representations of k as a sum of three squares (signs and
+    order counted), from the cube of the theta series sum_m q^(m^2)."""
+    r1 = np.zeros(kmax + 1, np.int64)
+    m = 0
+    while m * m <= kmax:
+        r1[m * m] += 1 if m == 0 else 2
+        m += 1
+    r2 = np.convolve(r1, r1)[: kmax + 1]
+    return np.convolve(r2, r1)[: kmax + 1]
+
+
+@pytest.mark.parametrize("sab", [1.0, 1.25, 1.5, 2.0, 2.5, 3.0, 4.0, 6.0, 8.0])
+def test_contact_shell_counts_and_symmetry(orc, sab):
+    """|S_ab| equals the number of lattice points with (s-1/2)^2 <= k < (s+1/2)^2
+    counted by the theta series, and the shell quadrature integrates the unit
+    sphere's first two moments exactly: sum s = 0, (4 pi/|S|) sum ss = (4 pi/3) I."""
+    d = orc.shell(sab).astype(float)
+    r3 = _r3(int((sab + 0.5) ** 2) + 1)
+    lo, hi = (sab - 0.5) ** 2, (sab + 0.5) ** 2
+    expect = sum(int(r3[k]) for k in range(1, len(r3)) if lo <= k < hi)
+    assert len(d) == expect
+    s = d / np.linalg.norm(d, axis=1)[:, None]
+    assert np.abs(s.sum(0)).max() < 1e-12
+    wS = 4 * math.pi / len(d)
+    assert np.allclose(wS * np.einsum("ka,kb->ab", s, s), 4 * math.pi / 3 * np.eye(3), atol=1e-12)
+
+
+@pytest.mark.parametrize("sab,lc", [(2.0, 2.5), (2.5, 2.5), (3.0, 2.5), (1.0, 3.0)])
+def test_attraction_set_counts(orc, sab, lc):
+    d = orc.attraction_set(sab, lc)
+    r3 = _r3(int((lc * sab) ** 2) + 1)
+    expect = sum(int(r3[k]) for k in range(len(r3)) if sab ** 2 <= k <= (lc * sab) ** 2)
+    assert len(d) == expect
+
+
+# ------------------------------------------------------------ BMCSL contact values
+def test_bmcsl_one_species_is_carnahan_starling(orc):
+    for sig in (1.0, 2.0, 3.7):
+        for eta in (0.0, 0.05, 0.2, 0.35, 0.5):
+            n = eta / (math.pi / 6 * sig ** 3)
+            xi2 = math.pi / 6 * n * sig ** 2
+            g = orc.bmcsl(sig, sig, xi2, eta)
+            cs = (1 - eta / 2) / (1 - eta) ** 3
+            assert abs(g - cs) < 1e-13 * cs
+
+
+def test_bmcsl_point_particle_limit(orc):
+    """A point particle (diameter -> 0) inserted into a hard-sphere fluid has
+    the exact scaled-particle contact value 1/(1 - xi3)."""
+    for xi2, xi3 in [(0.1, 0.2), (0.3, 0.45)]:
+        g = orc.bmcsl(2.0, 1e-12, xi2, xi3)
+        assert abs(g - 1 / (1 - xi3)) < 1e-10
+
+
+def test_bmcsl_virial_route_gives_bmcsl_equation_of_state(orc):
+    """Pressure from the virial route with these contact values,
+    beta P = sum n_a + (2 pi/3) sum_ab n_a n_b sigma_ab^3 g_ab,
+    equals the BMCSL equation of state
+    beta P = (6/pi)[xi0/(1-xi3) + 3 xi1 xi2/(1-xi3)^2 + (3-xi3) xi2^3/(1-xi3)^3]."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        S = rng.integers(2, 5)
+        sig = rng.uniform(0.5, 4.0, S)
+        n = rng.uniform(0.0, 1.0, S)
+        n *= rng.uniform(0.05, 0.5) / (math.pi / 6 * np.dot(n, sig ** 3))
+        xi = [math.pi / 6 * np.dot(n, sig ** k) for k in range(4)]
+        virial = n.sum()
+        for a in range(S):
+            for b in range(S):
+                sab = 0.5 * (sig[a] + sig[b])
+                virial += 2 * math.pi / 3 * n[a] * n[b] * sab ** 3 * orc.bmcsl(sig[a], sig[b], xi[2], xi[3])
+        o = 1 - xi[3]
+        eos = 6 / math.pi * (xi[0] / o + 3 * xi[1] * xi[2] / o ** 2 + (3 - xi[3]) * xi[2] ** 3 / o ** 3)
+        assert abs(virial - eos) < 1e-12 * eos
+
+
+def test_gfield_smoothing_of_uniform_state(orc):
+    """Uniform densities: n-bar = n, so g equals BMCSL at the bulk packing."""
+    lat, _ = W.binary_attraction((12, 10, 9))
+    n0 = W.densities_from_packing(0.3, lat.sigma, [0.5, 0.5])
+    n = np.repeat(n0[:, None], lat.nsites, axis=1)
+    g, xi, bad = orc.gfield(lat, n)
+    assert not bad
+    assert np.allclose(xi[1], 0.3, rtol=1e-14)
+    for a in range(2):
+        for b in range(2):
+            expect = orc.bmcsl(lat.sigma[a], lat.sigma[b], xi[0, 0], 0.3)
+            assert np.allclose(g[a, b], expect, rtol=1e-14)
+
+
+# ------------------------------------------------------------ equilibrium and forcing moments
+def _pop_moments(c, f):
+    """n, j, second moment of populations f[..., 19]."""
+    c = c.astype(float)
+    return f.sum(-1), np.einsum("...i,ia->...a", f, c), np.einsum("...i,ia,ib->...ab", f, c, c)
+
+
+def test_psi_perp_moments_match_eq_prefactor(orc):
+    """psi_perp of Eq. prefactor has density n^a, momentum n^a u^a, and
+    second moment n^a (kT/m I + u u + (u^a-u) u + u (u^a-u)) (its Gaussian
+    moments); the lattice populations must reproduce all three."""
+    lat = W.Lattice(shape=(3, 2, 2), sigma=[1.0, 1.5, 2.0], mass=[1.0, 1.0, 1.0])
+    rng = np.random.default_rng(3)
+    S, N = 3, lat.nsites
+    n = rng.uniform(0.02, 0.1, (S, N))
+    u = rng.uniform(-0.05, 0.05, (S, 3, N))
+    f = orc.init(lat, n, u)
+    c, _ = orc.velocities()
+    m0, m1, m2 = _pop_moments(c, np.transpose(f, (0, 2, 1)))
+    assert np.allclose(m0, n, rtol=1e-14)
+    assert np.allclose(m1, np.transpose(n[:, None, :] * u, (0, 2, 1)), atol=1e-16)
+    ub = (n[:, None, :] * u).sum(0) / n.sum(0)          # barycentric, equal masses
+    for a in range(S):
+        for r in range(N):
+            ua, uu = u[a, :, r], ub[:, r]
+            expect = n[a, r] * (CS2 * np.eye(3) + np.outer(uu, uu) + np.outer(ua - uu, uu) + np.outer(uu, ua - uu))
+            assert np.allclose(m2[a, r], expect, atol=1e-16)
+
+
+def _psi_perp_sites(orc, lat, n, u):
+    """psi_perp at M independent sites from the oracle's initialiser: [M][S][19]."""
+    M = n.shape[0]
+    f = np.zeros((M, lat.nspecies, 19))
+    for m in range(M):
+        f[m] = orc.init(lat, n[m][:, None].copy(), np.ascontiguousarray(u[m][:, :, None]))[:, :, 0]
+    return f
+
+
+def test_forcing_term_moments(orc):
+    """Forward-Euler forcing: from f = psi_perp one collision adds S_i; its
+    moments are those of (Phi/kT).(v-u) psi of Eq. evolution: 0, n a, n (u a + a u)."""
+    lat = W.Lattice(shape=(1, 1, 1), sigma=[1.0, 1.5], tau=0.8, force_scheme="explicit")
+    rng = np.random.default_rng(5)
+    M, S = 6, 2
+    n = rng.uniform(0.02, 0.1, (M, S))
+    u = rng.uniform(-0.05, 0.05, (M, S, 3))
+    j = n[..., None] * u
+    acc = rng.uniform(-1e-3, 1e-3, (M, S, 3))
+    f = _psi_perp_sites(orc, lat, n, u)
+    out = orc.collide_local(lat, f, n, j, acc)
+    c, _ = orc.velocities()
+    d0, d1, d2 = _pop_moments(c, out - f)
+    ub = j.sum(1) / n.sum(1)[:, None]
+    assert np.abs(d0).max() < 1e-17
+    assert np.allclose(d1, n[..., None] * acc, atol=1e-18)
+    expect = n[..., None, None] * (np.einsum("ma,msb->msab", ub, acc) + np.einsum("msa,mb->msab", acc, ub))
+    assert np.allclose(d2, expect, atol=1e-18)
+
+
+def test_semi_implicit_collision_moments(orc):
+    """Half-force shift: relaxing toward psi_perp at u + a/2 with the forcing
+    scaled by (1 - omega/2) keeps n and adds exactly n a to each species'
+    momentum, for any f (the shift and the scaling cancel in the first moment)."""
+    lat = W.Lattice(shape=(1, 1, 1), sigma=[1.0, 1.5, 2.0], tau=0.75)
+    rng = np.random.default_rng(8)
+    M, S = 5, 3
+    n = rng.uniform(0.02, 0.1, (M, S))
+    u = rng.uniform(-0.05, 0.05, (M, S, 3))
+    f = _psi_perp_sites(orc, lat, n, u) + rng.normal(0, 1e-4, (M, S, 19))
+    c, _ = orc.velocities()
+    nn, jj, _ = _pop_moments(c, f)
+    acc = rng.uniform(-1e-3, 1e-3, (M, S, 3))
+    out = orc.collide_local(lat, f, nn, jj, acc)
+    d0, d1, _ = _pop_moments(c, out - f)
+    assert np.abs(d0).max() < 1e-15 * nn.max()
+    assert np.allclose(d1, nn[..., None] * acc, atol=1e-17)
+
+
+def test_bgk_relaxes_nonequilibrium_stress_by_one_minus_omega(orc):
+    """Without force, collision conserves n and n u^a and multiplies the
+    non-equilibrium part of every non-conserved moment by (1 - omega)."""
+    tau = 0.7
+    lat = W.Lattice(shape=(1, 1, 1), sigma=[1.0, 1.5], tau=tau)
+    rng = np.random.default_rng(11)
+    M, S = 5, 2
+    n = rng.uniform(0.02, 0.1, (M, S))
+    u = rng.uniform(-0.05, 0.05, (M, S, 3))
+    feq = _psi_perp_sites(orc, lat, n, u)
+    c, _ = orc.velocities()
+    # a perturbation with zero density and momentum: random, projected
+    dp = rng.normal(0, 1e-4, (M, S, 19))
+    C = np.concatenate([np.ones((19, 1)), c.astype(float)], axis=1)
+    dp -= dp @ C @ np.linalg.solve(C.T @ C, C.T)
+    f = feq + dp
+    nn, jj, _ = _pop_moments(c, f)
+    out = orc.collide_local(lat, f, nn, jj, np.zeros((M, S, 3)))
+    assert np.allclose(out - feq, (1 - 1 / tau) * dp, atol=1e-17)
+
+
+# ------------------------------------------------------------ invariants of the full step
+def test_uniform_state_stays_uniform(orc):
+    lat, _ = W.binary_attraction((12, 12, 12))
+    n0 = W.densities_from_packing(0.3, lat.sigma, [0.5, 0.5])
+    n = np.repeat(n0[:, None], lat.nsites, axis=1)
+    f = orc.init(lat, n)
+    f0 = f.copy()
+    orc.step(lat, f, 5)
+    assert np.abs(f - f0).max() < 1e-15
+
+
+def test_mass_and_momentum_conservation_periodic(orc):
+    """Species mass is conserved exactly (sum psi_perp = n, sum S = 0) and,
+    with periodic boundaries and no external force, total momentum is
+    conserved because every pair force is antisymmetric (Eq. momentcomponent
+    summed over species)."""
+    lat, n = W.binary_attraction((16, 12, 10), seed=99)
+    u = W.random_velocities(lat, 0.02, seed=5)
+    f = orc.init(lat, n, u)
+    n0, j0 = orc.moments(lat, f)
+    M0, P0 = n0.sum(1), j0.sum((0, 2))
+    orc.step(lat, f, 20)
+    n1, j1 = orc.moments(lat, f)
+    assert np.abs(n1.sum(1) - M0).max() < 1e-13 * M0.max()
+    scale = n0.sum() * math.sqrt(CS2)
+    assert np.abs(j1.sum((0, 2)) - P0).max() < 1e-13 * scale
+    # the state did evolve
+    assert np.abs(j1 - j0).max() > 1e-6
+
+
+def test_forces_pairwise_antisymmetric(orc):
+    """sum_r sum_a n^a Phi^a = 0 for every random state (periodic box)."""
+    lat, _ = W.binary_attraction((11, 9, 13))
+    lat.sigma = [1.0, 1.5, 2.0]
+    S = 3
+    lat.mass = [1.0] * S
+    lat.eps = [[0.1, 0.05, 0.2], [0.05, 0.3, 0.1], [0.2, 0.1, 0.15]]
+    lat.lambda_c = [[2.0, 2.5, 2.2], [2.5, 1.8, 2.0], [2.2, 2.0, 2.5]]
+    rng = np.random.default_rng(1)
+    n = rng.uniform(0.01, 0.05, (S, lat.nsites))
+    j = n[:, None, :] * rng.uniform(-0.05, 0.05, (S, 3, lat.nsites))
+    phi, hc, vx, at = orc.forces(lat, n, j)
+    for part in (hc, vx, at):
+        tot = np.einsum("an,akn->k", n, part)
+        assert np.abs(tot).max() < 1e-14 * np.abs(n[:, None, :] * part).sum()
+
+
+# ------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("sigma", [[1.0, 1.5], [2.0, 3.0], [1.0, 1.25, 2.0]])
+def test_drag_matches_closed_form_gamma(orc, sigma):
+    """Uniform densities with uniform but different species velocities: the
+    effective field is Phi^a = -sum_b gamma^ab (u^a - u^b) with the closed form
+    gamma^ab = (8/3) sqrt(2 pi mu_ab kT) g_ab n^b sigma_ab^2 of Sec. III, and a
+    forward-Euler step changes each species' momentum by exactly n^a Phi^a."""
+    S = len(sigma)
+    lat = W.Lattice(shape=(9, 8, 7), sigma=list(sigma), tau=0.9, force_scheme="explicit")
+    n0 = W.densities_from_packing(0.25, sigma, [1.0 / S] * S)
+    N = lat.nsites
+    n = np.repeat(n0[:, None], N, axis=1)
+    uvec = np.array([[0.01, -0.02, 0.005], [-0.015, 0.01, 0.02], [0.0, 0.004, -0.01]])[:S]
+    u = np.repeat(uvec[:, :, None], N, axis=2)
+    f = orc.init(lat, n, u)
+    nn, j0 = orc.moments(lat, f)
+    phi, hc, vx, at = orc.forces(lat, nn, j0)
+    xi2 = math.pi / 6 * np.dot(n0, np.array(sigma) ** 2)
+    xi3 = math.pi / 6 * np.dot(n0, np.array(sigma) ** 3)
+    orc.step(lat, f, 1)
+    _, j1 = orc.moments(lat, f)
+    for a in range(S):
+        expect = np.zeros(3)
+        for b in range(S):
+            sab = 0.5 * (sigma[a] + sigma[b])
+            mu = 0.5
+            gab = orc.bmcsl(sigma[a], sigma[b], xi2, xi3)
+            gamma = 8.0 / 3.0 * math.sqrt(2 * math.pi * mu * lat.kT) * gab * n0[b] * sab ** 2
+            expect += -gamma * (uvec[a] - uvec[b])
+        assert np.allclose(phi[a], expect[:, None], rtol=1e-12, atol=1e-18)
+        assert np.abs(hc[a]).max() < 1e-15 and np.abs(at[a]).max() == 0.0
+        dj = (j1[a] - j0[a]).mean(axis=1)
+        assert np.allclose(dj, n0[a] * expect, rtol=1e-12, atol=1e-18)
+        assert np.abs(j1[a] - j1[a][:, :1]).max() < 1e-16
+
+
+def test_semi_implicit_uniform_drag_relaxation(orc):
+    """Uniform state, two species with different uniform velocities: with
+    uniform fields the velocity-exchange operator is linear with the constant
+    rates gamma^ab, so the semi-implicit step is a 2x2 (per component)
+    matrix recurrence written out here from its two passes; it conserves
+    the total momentum and relaxes u^A - u^B monotonically (no sign flip)."""
+    sigma = [1.0, 1.5]
+    lat = W.Lattice(shape=(6, 5, 4), sigma=sigma, tau=1.0)
+    n0 = W.densities_from_packing(0.2, sigma, [0.5, 0.5])
+    N = lat.nsites
+    n = np.repeat(n0[:, None], N, axis=1)
+    uvec = np.array([[0.01, 0.0, 0.0], [-0.01, 0.0, 0.0]])
+    f = orc.init(lat, n, np.repeat(uvec[:, :, None], N, axis=2))
+    xi2 = math.pi / 6 * np.dot(n0, np.array(sigma) ** 2)
+    xi3 = 0.2
+    G = np.zeros((2, 2))
+    for a in range(2):
+        for b in range(2):
+            sab = 0.5 * (sigma[a] + sigma[b])
+            G[a, b] = 8.0 / 3.0 * math.sqrt(2 * math.pi * 0.5 / 3) * orc.bmcsl(sigma[a], sigma[b], xi2, xi3) * n0[b] * sab ** 2
+    Gam = G.sum(1)
+    u = uvec[:, 0].copy()
+    w_prev = u[0] - u[1]
+    for step in range(5):
+        orc.step(lat, f, 1)
+        nn, jj = orc.moments(lat, f)
+        # pass 1: u* = (u + gain(u)/2) / (1 + Gamma/2), gain = G u
+        ust = (u + 0.5 * G @ u) / (1 + 0.5 * Gam)
+        # pass 2: a = G u* - Gamma u*
+        acc = G @ ust - Gam * ust
+        u = u + acc
+        got = jj[:, 0, :].mean(1) / n0
+        assert np.allclose(got, u, rtol=0, atol=1e-13 * 0.01)
+        assert abs(np.dot(n0, got)) < 1e-17
+        w = got[0] - got[1]
+        assert 0 < w < w_prev
+        w_prev = w
+
+
+# ------------------------------------------------------------ different algorithm: FFT
+def _fold_kernel(shape, offsets, values):
+    """Scatter kernel values at integer offsets into a periodic grid (z, y, x)."""
+    nx, ny, nz = shape
+    K = np.zeros((values.shape[1], nz, ny, nx))
+    for d, v in zip(offsets, values):
+        K[:, d[2] % nz, d[1] % ny, d[0] % nx] += v
+    return K
+
+
+def _correlate(field, K):
+    """out(r) = sum_d K(d) field(r + d) on the periodic grid, by FFT."""
+    F = np.fft.fftn(field)
+    return np.real(np.fft.ifftn(np.conj(np.fft.fftn(K, axes=(-3, -2, -1))) * F, axes=(-3, -2, -1)))
+
+
+def test_attraction_equals_fft_correlation_with_numerical_gradient(orc):
+    """G^ab(r) = -sum_r' n^b(r') grad U^ab(r - r') (Eq. potmeanforce) with
+    U = -eps (sigma_ab/|x|)^6 on sigma_ab <= |x| <= lambda_c sigma_ab: the
+    kernel is rebuilt here by central differences of U and the sum done by
+    FFT, on a box smaller than the interaction range (periodic images fold)."""
+    lat, n = W.binary_attraction((12, 10, 9), seed=3)
+    lat.eps = [[0.2, 0.1], [0.1, 0.3]]
+    lat.lambda_c = [[2.5, 2.0], [2.0, 2.2]]
+    S = 2
+    N = lat.nsites
+    j = np.zeros((S, 3, N))
+    phi, hc, vx, at = orc.forces(lat, n, j)
+    nx, ny, nz = lat.shape
+    h = 1e-5
+    for a in range(S):
+        G = np.zeros((3, nz, ny, nx))
+        for b in range(S):
+            sab = 0.5 * (lat.sigma[a] + lat.sigma[b])
+            rc = lat.lambda_c[a][b] * sab
+            e = lat.eps[a][b]
+            R = int(math.ceil(rc))
+            offs, vals = [], []
+            for dz in range(-R, R + 1):
+                for dy in range(-R, R + 1):
+                    for dx in range(-R, R + 1):
+                        x = np.array([dx, dy, dz], float)
+                        r = np.linalg.norm(x)
+                        if r == 0 or r < sab or r > rc:
+                            continue
+                        U = lambda y: -e * (sab / np.linalg.norm(y)) ** 6
+                        grad = np.array([(U(x + h * np.eye(3)[k]) - U(x - h * np.eye(3)[k])) / (2 * h) for k in range(3)])
+                        # contribution from r' = r + d: -grad U(r - r') = -grad U(-d) = +grad U(d)
+                        offs.append((dx, dy, dz))
+                        vals.append(grad)
+            K = _fold_kernel(lat.shape, offs, np.array(vals))
+            nb = n[b].reshape(nz, ny, nx)
+            G += _correlate(nb[None], K)
+        got = at[a].reshape(3, nz, ny, nx)
+        assert np.allclose(got, G, rtol=0, atol=1e-8 * np.abs(G).max())
+        assert np.abs(G).max() > 1e-4
+
+
+def _shell_offsets(sab):
+    R = int(math.ceil(sab + 0.5))
+    out = []
+    for dz in range(-R, R + 1):
+        for dy in range(-R, R + 1):
+            for dx in range(-R, R + 1):
+                r = math.sqrt(dx * dx + dy * dy + dz * dz)
+                if r > 0 and sab - 0.5 <= r < sab + 0.5:
+                    out.append((dx, dy, dz))
+    return np.array(out)
+
+
+def test_contact_terms_equal_fft_split(orc):
+    """The hard-core and velocity-exchange sums of Eqs. potmeanforce and
+    viscousforce are bilinear in (g, n, u); with the symmetric pair value
+    (g(r)+g(r+d))/2 they split into linear correlations of n, g n, j, g j
+    with the vector kernel s and tensor kernel s s, evaluated here by FFT."""
+    rng = np.random.default_rng(17)
+    lat = W.Lattice(shape=(10, 9, 8), sigma=[1.0, 2.0], tau=1.0)
+    S, N = 2, lat.nsites
+    n0 = W.densities_from_packing(0.25, lat.sigma, [0.5, 0.5])
+    n = n0[:, None] * (1 + 0.2 * rng.uniform(-1, 1, (S, N)))
+    u = rng.uniform(-0.05, 0.05, (S, 3, N))
+    j = n[:, None, :] * u
+    phi, hc, vx, at = orc.forces(lat, n, j)
+    g, _, _ = orc.gfield(lat, n)
+    nx, ny, nz = lat.shape
+    sh = (nz, ny, nx)
+    for a in range(S):
+        Fhc = np.zeros((3,) + sh)
+        Fv = np.zeros((3,) + sh)
+        for b in range(S):
+            sab = 0.5 * (lat.sigma[a] + lat.sigma[b])
+            d = _shell_offsets(sab).astype(float)
+            s = d / np.linalg.norm(d, axis=1)[:, None]
+            wS = 4 * math.pi / len(d)
+            Kv = _fold_kernel(lat.shape, d.astype(int), s)                               # [3]
+            Kt = _fold_kernel(lat.shape, d.astype(int), np.einsum("ka,kb->kab", s, s).reshape(-1, 9)).reshape((3, 3) + sh)
+            gab = g[a, b].reshape(sh)
+            nb = n[b].reshape(sh)
+            jb = j[b].reshape((3,) + sh)
+            ua = u[a].reshape((3,) + sh)
+            # hard core: -kT s^2 wS sum_d s (g(r)+g(r+d))/2 n(r+d)
+            Cn = _correlate(nb[None], Kv)
+            Cgn = _correlate((gab * nb)[None], Kv)
+            Fhc += -lat.kT * sab ** 2 * wS * 0.5 * (gab * Cn + Cgn)
+            # velocity exchange: K wS sum_d s s.(j(r+d) - n(r+d) u^a(r)) (g(r)+g(r+d))/2
+            Kab = 2 * sab ** 2 * math.sqrt(2 * 0.5 * lat.kT / math.pi)
+            Tj = sum(_correlate(jb[q][None], Kt[:, q]) for q in range(3))
+            Tgj = sum(_correlate((gab * jb[q])[None], Kt[:, q]) for q in range(3))
+            Tn = _correlate(nb[None], Kt.reshape((9,) + sh)).reshape((3, 3) + sh)
+            Tgn = _correlate((gab * nb)[None], Kt.reshape((9,) + sh)).reshape((3, 3) + sh)
+            term_u = np.einsum("ab...,b...->a...", 0.5 * (gab * Tn + Tgn), ua)
+            Fv += Kab * wS * (0.5 * (gab * Tj + Tgj) - term_u)
+        assert np.allclose(hc[a].reshape((3,) + sh), Fhc, rtol=0, atol=1e-13 * np.abs(Fhc).max())
+        assert np.allclose(vx[a].reshape((3,) + sh), Fv, rtol=0, atol=1e-12 * np.abs(Fv).max())
+
+
+# ------------------------------------------------------------ walls
+def test_couette_profile_between_moving_walls(orc):
+    """Near-ideal gas between halfway bounce-back walls at y = -1/2 and
+    y = L - 1/2 moving at U_lo, U_hi: the steady velocity is the linear
+    Couette profile u_x = U_lo + (U_hi - U_lo)(y + 1/2)/L; mass is conserved."""
+    L = 8
+    lat = W.Lattice(shape=(2, L, 2), sigma=[1.0, 1.5], tau=1.0, wall_axis=1,
+                    wall_u_lo=(-0.02, 0.0, 0.0), wall_u_hi=(0.03, 0.0, 0.0))
+    n = np.full((2, lat.nsites), 1e-5)
+    f = orc.init(lat, n)
+    M0 = f.sum()
+    orc.step(lat, f, 2500)
+    nn, jj = orc.moments(lat, f)
+    assert abs(f.sum() - M0) < 1e-12 * M0
+    ux = (jj[:, 0].sum(0) / nn.sum(0)).reshape(2, L, 2)[0, :, 0]
+    y = np.arange(L)
+    expect = -0.02 + 0.05 * (y + 0.5) / L
+    assert np.abs(ux - expect).max() < 1e-3 * 0.05
