@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Throughput of the multispecies Enskog/RPA lattice Boltzmann step on GB300.
+
+Workload (default): binary hard-sphere mixture sigma = (1, 1.5), packing 0.2,
+equal mole fractions, tau = 1, no attraction, 5% concentration sine wave
+along x (Eq. perturba) on a 256^3 periodic D3Q19 lattice, FP32 populations.
+One "step" is one full time step of the method (moments, contact values,
+both force passes, collision, streaming) over the whole lattice.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlb|reference]
+
+Prints one JSON line.  value = MLUPS per species over all ranks (species-site
+updates per microsecond); each rank runs an independent replica (weak scaling,
+no data-path collective).  --impl reference times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS/species + % HBM roofline; surrogate/BF16 speedup at <=1% D_mutual error"
+UNIT = "MLUPS/species"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["mlb", "reference"], default="mlb")
+    ap.add_argument("--size", type=int, default=256, help="cubic lattice extent")
+    ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample extent for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(size):
+    from paper_1105_3634_gb300 import workloads as W
+    lat, n = W.binary_config1((size, size, size))
+    return lat, n
+
+
+def config_dict(size):
+    return {"workload": f"binary hard spheres sigma=(1,1.5), packing 0.2, tau=1, 5% sine wave, {size}^3 periodic D3Q19",
+            "grid": [size, size, size], "species": 2, "lattice": "D3Q19", "precision": "FP32 populations",
+            "force_scheme": "semi-implicit half-force shift",
+            "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (2 * 19 * 4 * size ** 3 / 1e9),
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ per-kernel algorithmic bytes
+def algorithmic_bytes(kernel, S, npairs, has_fext=False):
+    """Bytes per species-site that the kernel must move by design."""
+    g = 4.0 * npairs / S
+    return {
+        "k_moments": 76 + 16,                                  # f read, (dn, j) write
+        "k_gfield": 4 + g,                                     # dn read, g write
+        "k_pass1": 16 + g + 12 + 12 + (12 if has_fext else 0),  # moments, g read; frest, du write
+        "k_pass2_collide": 76 + 16 + g + 12 + 12 + 76,         # f, moments, g, frest, du read; f write
+    }[kernel]
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = (uuid or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and self.uuid not in parts[1].lower():
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ cpu baseline (oracle)
+def cpu_baseline(size, steps=2):
+    import numpy as np
+    import oracle
+    oracle.build()
+    lat, n = workload(size)
+    f = oracle.init(lat, n)
+    oracle.step(lat, f, 1)                    # warm (page-in, thread pool)
+    t0 = time.perf_counter()
+    oracle.step(lat, f, steps)
+    dt = time.perf_counter() - t0
+    value = lat.nspecies * lat.nsites * steps / dt / 1e6
+    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{size}^3 lattice of the same physics, {steps} timed steps after 1 warm step, FP64 C oracle, OpenMP"}
+
+
+# ------------------------------------------------------------------ the GPU arm
+def run_mlb(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_1105_3634_gb300 import build as B
+    B.build()
+    from paper_1105_3634_gb300 import mlb
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    lat, n = workload(args.size)
+    S, N = lat.nspecies, lat.nsites
+    stream = torch.cuda.Stream(device=dev)
+    sim = mlb.Simulation(lat, stream=stream)
+    sim.set_fields(n)
+    sim.step(args.warmup)
+    sim.synchronize()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = ""
+    clocks = Clocks(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    sim.profile(True)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    sim.step(args.steps)
+    t_end.record(stream)
+    sim.synchronize()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_total = t_start.elapsed_time(t_end)
+    prof = sim.profile_read()
+    sim.profile(False)
+    if dist:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * S * N * args.steps / (ms_total * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: upload the fields, then
+    # every step a device->host read of the conservation sums (the monitored
+    # metric), finally the moments back to the host
+    e2e = None
+    if not args.no_e2e:
+        nh = torch.empty((S, N), dtype=torch.float64, pin_memory=True).numpy()
+        nh[:] = n
+        n_out = torch.empty((S, N), dtype=torch.float64, pin_memory=True).numpy()
+        u_out = torch.empty((S, 3, N), dtype=torch.float64, pin_memory=True).numpy()
+        sim.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        sim.set_fields(nh)
+        for _ in range(args.steps):
+            sim.step(1)
+            sim.conservation()
+        sim.moments(n_out, u_out)
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = nh.nbytes / args.steps
+        d2h = (S + 3) * 8 + (n_out.nbytes + u_out.nbytes) / args.steps
+        e2e = {"value": world * S * N * args.steps / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "what": "mlb_set_fields from pinned host n, K x (mlb_step(1) + mlb_conservation), mlb_get_moments"}
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    npairs = S * (S + 1) // 2
+    peak, peak_kind = measured_peak_hbm()
+    kernels = {}
+    for name, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        per_launch_ms = ms / cnt
+        b = algorithmic_bytes(name, S, npairs) * S * N
+        kernels[name] = {"launches": cnt, "ms_total": ms, "ms_per_launch": per_launch_ms,
+                         "share": ms / sum(v[0] for v in prof.values()),
+                         "algorithmic_bytes_per_launch": b, "achieved_gbs": b / (per_launch_ms * 1e-3) / 1e9}
+    top = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    roof = {"kernel": top, "bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak,
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "unit": "GB/s", "frac": kernels[top]["achieved_gbs"] / peak, "traffic": None}
+    step_bytes = 184.0 * S * N
+    step_roof = {"bytes_per_species_site": 184, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
+                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sine-wave mixture)",
+           "config": config_dict(args.size), "roofline": roof, "step_roofline": step_roof,
+           "kernels": kernels, "gpu_launches": sim.launches_per_step() * args.steps * 1,
+           "mlups": value / S, "clocks": clk, "e2e": e2e}
+    sim.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step is one oracle
+    time step of a bounded sample (96^3) of the same workload."""
+    import oracle
+    oracle.build()
+    size = min(args.size, 96)
+    lat, n = workload(size)
+    f = oracle.init(lat, n)
+    if args.warmup:
+        oracle.step(lat, f, args.warmup)
+    t0 = time.perf_counter()
+    oracle.step(lat, f, args.steps)
+    dt = time.perf_counter() - t0
+    value = lat.nspecies * lat.nsites * args.steps / dt / 1e6
+    cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"{size}^3 lattice of the same physics per step (bounded sample of {args.size}^3), FP64 C oracle"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded sine-wave mixture)", "config": config_dict(args.size),
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    out = run_mlb(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

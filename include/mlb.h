@@ -1,0 +1,167 @@
+/*
+ * mlb.h -- C ABI of the GB300 (sm_103a) multispecies Enskog/RPA lattice
+ * Boltzmann step of Marini Bettolo Marconi & Melchionna, "Multicomponent
+ * Diffusion in Nanosystems" (arXiv:1105.3634).
+ *
+ * One time step advances the D3Q19 populations f^a_i of every species a by
+ *   moments      n^a = sum_i f^a_i, n^a u^a = sum_i c_i f^a_i        (Sec. II, Eq. colonna)
+ *   contact g    g_ab = BMCSL contact value of the densities smoothed over
+ *                a ball of radius kappa sigma_c                    (Sec. II, "smoothing procedure")
+ *   field        Phi^a = F^hc + G + F^drag + F^visc                (Sec. III, Eqs. splitforce,
+ *                                                                   potmeanforce, gammaab, viscousforce)
+ *   collide      f - omega (f - psi_perp) + forcing                (Sec. II, Eqs. evolution, prefactor)
+ *   stream       f_i(r + c_i, t + 1), periodic or halfway bounce-back walls
+ * in FP32 on the GPU.  The contact-sphere integrals are sums over the lattice
+ * shell sigma_ab - 1/2 <= |d| < sigma_ab + 1/2 with weight 4 pi/|shell|; the
+ * attraction is U_ab = -eps_ab (sigma_ab/r)^6 on sigma_ab <= r <= lambda_c sigma_ab.
+ * The force enters with a semi-implicit half-force shift (psi_perp and the
+ * forcing evaluated at u + a/2, forcing scaled by 1 - omega/2) unless
+ * MLB_FORCE_EXPLICIT is set.
+ *
+ * Conventions
+ *   - Units: lattice spacing = time step = 1; every mass must be 1 and kT = 1/3
+ *     (the D3Q19 sound speed squared).
+ *   - Site index: x + nx * (y + ny * z)  (x fastest).
+ *   - Host arrays are owned by the caller and only read or written during the
+ *     call.  All device memory is owned by the context; it is obtained once in
+ *     mlb_create from desc->dev_alloc (or cudaMalloc when NULL) and released by
+ *     mlb_destroy.
+ *   - Every function returns an mlb_status and never aborts.  After
+ *     MLB_ECUDA, MLB_ENUMERIC or MLB_ETIMEOUT the context is failed: later
+ *     calls return MLB_ESTATE until mlb_destroy.  mlb_last_error() gives a
+ *     one-line reason.
+ *   - mlb_step is asynchronous on the context's stream; the mlb_get_* and
+ *     mlb_conservation calls synchronise that stream.
+ *   - One context per host thread at a time.
+ */
+#ifndef MLB_H
+#define MLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLB_Q 19                 /* D3Q19 velocities */
+#define MLB_MAX_SPECIES 4
+
+typedef struct mlb_ctx mlb_ctx;
+
+typedef enum {
+    MLB_OK = 0,
+    MLB_EINVAL = 1,    /* invalid argument or state (message says which) */
+    MLB_ENOMEM = 2,    /* device allocation failed */
+    MLB_ECUDA = 3,     /* a CUDA call failed */
+    MLB_ENUMERIC = 4,  /* NaN/Inf met, or packing xi3 >= 1 somewhere */
+    MLB_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    MLB_ESTATE = 6     /* context failed earlier, or call made out of order */
+} mlb_status;
+
+/* flags */
+#define MLB_DRAG_ONLY       1u   /* partner velocity at r: Eq. gammaab alone, no viscous part */
+#define MLB_FORCE_EXPLICIT  2u   /* forward-Euler forcing at u (no half-force shift) */
+
+typedef struct {
+    int32_t nx, ny, nz;          /* lattice extents, each >= 1 */
+    int32_t nspecies;            /* 1 .. MLB_MAX_SPECIES */
+    int32_t wall_axis;           /* -1: periodic; 0/1/2: halfway bounce-back walls normal to that
+                                    axis at coordinates -1/2 and n-1/2 */
+    uint32_t flags;              /* MLB_* flags */
+    double wall_u_lo[3];         /* velocity of the wall at coordinate -1/2 (tangential) */
+    double wall_u_hi[3];         /* velocity of the wall at coordinate n-1/2 (tangential) */
+    double tau;                  /* BGK relaxation time (omega = 1/tau), > 1/2 */
+    double kT;                   /* must be 1/3 */
+    double kappa;                /* smoothing-ball radius / sigma_cc (0.5 by default if 0) */
+    /* device allocator: returns a device pointer aligned to 256 bytes, or NULL.
+       NULL function pointers select cudaMalloc/cudaFree. */
+    void *(*dev_alloc)(size_t bytes, void *user);
+    void (*dev_free)(void *ptr, void *user);
+    void *alloc_user;
+    void *stream;                /* cudaStream_t the context launches on; NULL = a stream the
+                                    context creates and owns */
+} mlb_lattice_desc;
+
+/* Create a context: validates desc, allocates every device buffer.  The
+ * context then needs mlb_set_species, optionally mlb_set_interactions, and
+ * mlb_set_fields (or mlb_set_populations) before mlb_step.
+ * Errors: MLB_EINVAL (bad extents, tau <= 1/2, kT != 1/3, wall velocity with a
+ * normal component), MLB_ENOMEM, MLB_ECUDA. */
+mlb_status mlb_create(const mlb_lattice_desc *desc, mlb_ctx **out);
+
+/* Hard-sphere diameters sigma_aa (Sec. III: sigma_ab = (sigma_aa + sigma_bb)/2)
+ * and masses, each array of nspecies doubles.  Requires sigma >= 1 and every
+ * mass == 1.  Builds the contact shells and smoothing balls.
+ * Errors: MLB_EINVAL, also when a stencil offset reaches a full periodic
+ * extent (every periodic extent must exceed the largest offset component). */
+mlb_status mlb_set_species(mlb_ctx *ctx, const double *sigma, const double *mass);
+
+/* Attractive tails (Sec. III, G term of Eq. potmeanforce; RPA, g = 1 inside):
+ * eps[a*S+b] = eps_ab >= 0 (symmetric), lambda_c[a*S+b] = cutoff / sigma_ab
+ * (symmetric, >= 1).  eps = NULL switches the attraction off.
+ * Errors: MLB_EINVAL (asymmetric, negative, non-finite, table too large). */
+mlb_status mlb_set_interactions(mlb_ctx *ctx, const double *eps, const double *lambda_c);
+
+/* Initial state f := psi_perp(n, u) (Eq. prefactor at the given fields).
+ * n: [S][N] number densities (>= 0, finite);  u: [S][3][N] species velocities
+ * or NULL for rest.  Also fixes the per-species reference density n_ref^a
+ * (the mean of n^a) that the FP32 populations are stored relative to.
+ * Errors: MLB_EINVAL (negative or non-finite n, |u| >= 1, packing xi3 >= 1). */
+mlb_status mlb_set_fields(mlb_ctx *ctx, const double *n, const double *u);
+
+/* Per-site external body force F^a (Eq. evolution) in lattice units:
+ * fext: [S][3][N], or NULL to remove it. */
+mlb_status mlb_set_external_force(mlb_ctx *ctx, const double *fext);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the context's stream). */
+mlb_status mlb_step(mlb_ctx *ctx, int64_t nsteps);
+
+/* Wait for the context's stream; reports numeric faults found by the steps. */
+mlb_status mlb_synchronize(mlb_ctx *ctx);
+
+/* Moments of the current populations: n [S][N] and u [S][3][N] (u^a = j^a/n^a,
+ * or the barycentric velocity where n^a is below 1e-12).  Either may be NULL. */
+mlb_status mlb_get_moments(mlb_ctx *ctx, double *n, double *u);
+
+/* Acceleration a^a = (Phi^a + F^a)/m^a the next step applies to the current
+ * state: [S][3][N].  With the half-force shift it is F^hc + G + F^a plus the
+ * velocity-exchange force at u* = u + du, where du solves
+ * (I + Gamma/2) du = (F^hc + G + F^a + F^v(u))/2 at each site (one Jacobi
+ * sweep of u* = u + a(u*)/2; Gamma = the local friction matrix). */
+mlb_status mlb_get_acceleration(mlb_ctx *ctx, double *acc);
+
+/* FP64 global sums of the current state: mass[a] = sum_r n^a (S doubles),
+ * mom[3] = sum_a m^a sum_r j^a.  Returns MLB_ENUMERIC if any moment is NaN/Inf. */
+mlb_status mlb_conservation(mlb_ctx *ctx, double *mass, double *mom);
+
+/* Raw FP32 populations as stored: fdev[a][i][r] = f^a_i(r) - w_i n_ref^a, in the
+ * velocity order of mlb_velocity_set, plus n_ref [S] and the step counter.
+ * Any output pointer may be NULL.  set restores them bit for bit. */
+mlb_status mlb_get_populations(mlb_ctx *ctx, float *fdev, double *nref, int64_t *step);
+mlb_status mlb_set_populations(mlb_ctx *ctx, const float *fdev, const double *nref, int64_t step);
+
+/* The D3Q19 velocity set the populations use: c[19][3] and weights w[19]. */
+mlb_status mlb_velocity_set(int32_t *c, double *w);
+
+/* Number of kernel launches one mlb_step(1) issues with the current settings. */
+int32_t mlb_launches_per_step(const mlb_ctx *ctx);
+
+/* Instrumentation (no counterpart in the paper).  While enabled, mlb_step
+ * records a CUDA event pair around every kernel launch on the context's
+ * stream.  mlb_profile_read synchronises, then returns per kernel kind k
+ * (0 .. count-1, named by mlb_kernel_name) the summed device time in
+ * milliseconds and the number of launches since the last read, and resets
+ * them.  Arrays hold max_kernels entries; returns the number of kinds. */
+mlb_status mlb_profile_enable(mlb_ctx *ctx, int32_t enable);
+int32_t mlb_profile_read(mlb_ctx *ctx, double *ms, int64_t *launches, int32_t max_kernels);
+const char *mlb_kernel_name(int32_t k);
+
+const char *mlb_last_error(const mlb_ctx *ctx);
+const char *mlb_status_string(mlb_status s);
+void mlb_destroy(mlb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLB_H */

@@ -262,9 +262,13 @@ def num_threads() -> int:
 
 
 def velocity_fields(lat, n, j):
-    """Species velocities u^a = j^a / n^a (R1): [S][3][N]."""
+    """Species velocities (R1): u^a = j^a / n^a, and the barycentric velocity
+    u = sum_a m^a j^a / sum_a m^a n^a where n^a vanishes.  [S][3][N]."""
+    m = np.asarray(lat.mass, np.float64)
+    rho = np.einsum("a,an->n", m, n)
     with np.errstate(divide="ignore", invalid="ignore"):
-        u = np.where(n[:, None, :] > 1e-300, j / n[:, None, :], 0.0)
+        ub = np.where(rho > 0, np.einsum("a,akn->kn", m, j) / rho, 0.0)
+        u = np.where(n[:, None, :] > 1e-300, j / n[:, None, :], ub[None, :, :])
     return u
 
 

@@ -1,0 +1,702 @@
+// mlb_api.cu -- the C ABI declared in include/mlb.h: context, validation,
+// stencil tables, device memory and the launch sequence of one time step.
+#include "mlb.h"
+#include "mlb_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr int kTableCap = 16384;               // stencil entries per context (256 KiB)
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kCs2 = 1.0 / 3.0;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct mlb_ctx {
+    mlb_lattice_desc desc{};
+    mlbi_params p{};
+    mlbi_buffers b{};
+    void *slab = nullptr;
+    size_t slab_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int cur = 0;
+    int64_t step = 0;
+    bool species_set = false, fields_set = false;
+    bool failed = false;
+    std::string err;
+    std::vector<double> sigma, mass, eps, lambda_c, nref;
+    std::vector<mlbi_entry> table;
+    int max_offset = 1;                         // largest stencil offset component
+    // instrumentation: one event pair per recorded launch
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;                   // kernel kind of pair k
+    size_t ev_used = 0;
+    double prof_ms[8] = {0};
+    int64_t prof_count[8] = {0};
+};
+
+namespace {
+
+mlb_status fail(mlb_ctx *c, mlb_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    if (s == MLB_ECUDA || s == MLB_ENUMERIC || s == MLB_ETIMEOUT) c->failed = true;
+    return s;
+}
+
+mlb_status cuda_check(mlb_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return MLB_OK;
+    return fail(c, MLB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MLB_GUARD(ctx)                                                                     \
+    do {                                                                                   \
+        if (!(ctx)) return MLB_EINVAL;                                                     \
+        if ((ctx)->failed) return MLB_ESTATE;                                              \
+    } while (0)
+
+#define MLB_CUDA(ctx, call)                                                                \
+    do {                                                                                   \
+        mlb_status st_ = cuda_check((ctx), (call), #call);                                 \
+        if (st_ != MLB_OK) return st_;                                                     \
+    } while (0)
+
+double bmcsl(double sa, double sb, double xi2, double xi3)
+{
+    double h = sa * sb / (sa + sb), o = 1.0 - xi3;
+    return 1.0 / o + 3.0 * h * xi2 / (o * o) + 2.0 * h * h * xi2 * xi2 / (o * o * o);
+}
+
+// canonical half of the +-d pairs: first non-zero of (dz, dy, dx) positive
+bool canonical(int dx, int dy, int dz)
+{
+    return dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+}
+
+// Rebuild every stencil table and the parameter block from species,
+// interactions and reference densities.
+mlb_status rebuild(mlb_ctx *c)
+{
+    const int S = c->desc.nspecies;
+    mlbi_params &p = c->p;
+    std::vector<mlbi_entry> tab;
+    int maxoff = 1;
+    auto push = [&](int dx, int dy, int dz, double vx, double vy, double vz) {
+        mlbi_entry e;
+        e.x = (float)vx; e.y = (float)vy; e.z = (float)vz;
+        int packed = mlbi_pack(dx, dy, dz);
+        std::memcpy(&e.w, &packed, sizeof(int));
+        tab.push_back(e);
+        maxoff = std::max(maxoff, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
+    };
+    // smoothing balls |d| <= kappa sigma_c (origin included)
+    for (int g = 0; g < S; ++g) {
+        double R = c->desc.kappa * c->sigma[g];
+        int Ri = (int)std::floor(R) + 1;
+        p.ball_start[g] = (int)tab.size();
+        for (int dz = -Ri; dz <= Ri; ++dz)
+            for (int dy = -Ri; dy <= Ri; ++dy)
+                for (int dx = -Ri; dx <= Ri; ++dx)
+                    if ((double)(dx * dx + dy * dy + dz * dz) <= R * R) push(dx, dy, dz, 0, 0, 0);
+        p.ball_count[g] = (int)tab.size() - p.ball_start[g];
+        p.ball_inv[g] = 1.0f / (float)p.ball_count[g];
+    }
+    // pairs
+    int np = 0;
+    bool attraction = false;
+    double xi2 = 0.0, xi3 = 0.0;
+    for (int g = 0; g < S; ++g) {
+        xi2 += kPi / 6.0 * c->sigma[g] * c->sigma[g] * c->nref[g];
+        xi3 += kPi / 6.0 * c->sigma[g] * c->sigma[g] * c->sigma[g] * c->nref[g];
+    }
+    for (int a = 0; a < S; ++a)
+        for (int b = a; b < S; ++b) {
+            mlbi_pair &pr = p.pair[np];
+            const double sab = 0.5 * (c->sigma[a] + c->sigma[b]);
+            const double lo = sab - 0.5, hi = sab + 0.5;
+            const int Ri = (int)std::ceil(hi) + 1;
+            pr.shell_start = (int)tab.size();
+            for (int dz = -Ri; dz <= Ri; ++dz)
+                for (int dy = -Ri; dy <= Ri; ++dy)
+                    for (int dx = -Ri; dx <= Ri; ++dx) {
+                        const double q = (double)(dx * dx + dy * dy + dz * dz);
+                        if (q == 0.0 || !canonical(dx, dy, dz)) continue;
+                        if (q < (lo > 0 ? lo * lo : 0.0) || !(q < hi * hi)) continue;
+                        const double len = std::sqrt(q);
+                        push(dx, dy, dz, dx / len, dy / len, dz / len);
+                    }
+            pr.shell_count = (int)tab.size() - pr.shell_start;
+            const double wS = 4.0 * kPi / (2.0 * pr.shell_count);
+            const double mu = c->mass[a] * c->mass[b] / (c->mass[a] + c->mass[b]);
+            pr.hc_pre = (float)(c->desc.kT * sab * sab * wS);
+            pr.vx_pre = (float)(2.0 * sab * sab * std::sqrt(2.0 * mu * c->desc.kT / kPi) * wS);
+            pr.h = (float)(c->sigma[a] * c->sigma[b] / (c->sigma[a] + c->sigma[b]));
+            pr.g_ref = (float)bmcsl(c->sigma[a], c->sigma[b], xi2, xi3);
+            // attraction: K(d) = 6 eps sigma^6 d / |d|^8 on sigma <= |d| <= lambda_c sigma
+            pr.attr_start = (int)tab.size();
+            const double e = c->eps.empty() ? 0.0 : c->eps[a * S + b];
+            if (e != 0.0) {
+                attraction = true;
+                const double rc = c->lambda_c[a * S + b] * sab;
+                const int Rc = (int)std::ceil(rc) + 1;
+                const double s6 = std::pow(sab, 6.0);
+                for (int dz = -Rc; dz <= Rc; ++dz)
+                    for (int dy = -Rc; dy <= Rc; ++dy)
+                        for (int dx = -Rc; dx <= Rc; ++dx) {
+                            const double q = (double)(dx * dx + dy * dy + dz * dz);
+                            if (q == 0.0 || !canonical(dx, dy, dz)) continue;
+                            if (q < sab * sab || q > rc * rc) continue;
+                            const double k = 6.0 * e * s6 / (q * q * q * q);
+                            push(dx, dy, dz, k * dx, k * dy, k * dz);
+                        }
+            }
+            pr.attr_count = (int)tab.size() - pr.attr_start;
+            p.pair_index[a][b] = p.pair_index[b][a] = np;
+            ++np;
+        }
+    if ((int)tab.size() > kTableCap)
+        return fail(c, MLB_EINVAL, "stencil tables need %zu entries, capacity is %d (reduce sigma or lambda_c)",
+                    tab.size(), kTableCap);
+    const int L[3] = {c->desc.nx, c->desc.ny, c->desc.nz};
+    for (int ax = 0; ax < 3; ++ax)
+        if (ax != c->desc.wall_axis && L[ax] <= maxoff)
+            return fail(c, MLB_EINVAL,
+                        "periodic extent %d along axis %d must exceed the largest stencil offset %d", L[ax], ax,
+                        maxoff);
+    p.npairs = np;
+    p.has_attraction = attraction ? 1 : 0;
+    p.xi2_ref = (float)xi2;
+    p.xi3_ref = (float)xi3;
+    for (int g = 0; g < S; ++g) {
+        p.nref[g] = (float)c->nref[g];
+        p.xi2_coef[g] = (float)(kPi / 6.0 * c->sigma[g] * c->sigma[g]);
+        p.xi3_coef[g] = (float)(kPi / 6.0 * c->sigma[g] * c->sigma[g] * c->sigma[g]);
+    }
+    c->table = tab;
+    c->max_offset = maxoff;
+    MLB_CUDA(c, cudaMemcpyAsync((void *)c->b.table, tab.data(), tab.size() * sizeof(mlbi_entry),
+                                cudaMemcpyHostToDevice, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MLB_OK;
+}
+
+mlb_status check_flags(mlb_ctx *c)
+{
+    unsigned int fl = 0;
+    MLB_CUDA(c, cudaMemcpyAsync(&fl, c->b.flags, sizeof fl, cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (fl & MLBI_FLAG_NAN) return fail(c, MLB_ENUMERIC, "non-finite moments met (the state diverged)");
+    if (fl & MLBI_FLAG_XI3) return fail(c, MLB_ENUMERIC, "packing fraction xi3 >= 1 met at some site");
+    return MLB_OK;
+}
+
+mlb_status require_ready(mlb_ctx *c)
+{
+    if (!c->species_set) return fail(c, MLB_ESTATE, "mlb_set_species has not been called");
+    if (!c->fields_set) return fail(c, MLB_ESTATE, "no state: call mlb_set_fields or mlb_set_populations");
+    return MLB_OK;
+}
+
+enum { K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_NKINDS = 4 };
+const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2_collide"};
+
+// event pair around one launch when profiling
+struct Timed {
+    mlb_ctx *c;
+    size_t k = (size_t)-1;
+    Timed(mlb_ctx *ctx, int kind) : c(ctx)
+    {
+        if (!c->profiling) return;
+        if (c->ev_used * 2 + 2 > c->ev_pool.size()) {
+            cudaEvent_t e0, e1;
+            if (cudaEventCreate(&e0) != cudaSuccess) return;
+            if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+            c->ev_pool.push_back(e0);
+            c->ev_pool.push_back(e1);
+            c->ev_kind.push_back(kind);
+        }
+        k = c->ev_used++;
+        c->ev_kind[k] = kind;
+        cudaEventRecord(c->ev_pool[2 * k], c->stream);
+    }
+    ~Timed()
+    {
+        if (k != (size_t)-1) cudaEventRecord(c->ev_pool[2 * k + 1], c->stream);
+    }
+};
+
+// The force passes of one step on the current populations.
+mlb_status forces(mlb_ctx *c)
+{
+    { Timed t(c, K_MOMENTS); MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream)); }
+    { Timed t(c, K_GFIELD); MLB_CUDA(c, mlbi_launch_gfield(c->p, c->b, c->stream)); }
+    { Timed t(c, K_PASS1); MLB_CUDA(c, mlbi_launch_pass1(c->p, c->b, c->stream)); }
+    return MLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mlb_status_string(mlb_status s)
+{
+    switch (s) {
+    case MLB_OK: return "ok";
+    case MLB_EINVAL: return "invalid argument";
+    case MLB_ENOMEM: return "out of device memory";
+    case MLB_ECUDA: return "CUDA error";
+    case MLB_ENUMERIC: return "numeric fault";
+    case MLB_ETIMEOUT: return "device wait timed out";
+    case MLB_ESTATE: return "context not usable";
+    }
+    return "unknown status";
+}
+
+mlb_status mlb_velocity_set(int32_t *cv, double *w)
+{
+    static const int C[MLBI_Q][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                      {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                      {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                      {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    for (int i = 0; i < MLBI_Q; ++i) {
+        if (cv)
+            for (int k = 0; k < 3; ++k) cv[3 * i + k] = C[i][k];
+        if (w) w[i] = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    return MLB_OK;
+}
+
+mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
+{
+    if (!d || !out) return MLB_EINVAL;
+    *out = nullptr;
+    mlb_ctx *c = new (std::nothrow) mlb_ctx();
+    if (!c) return MLB_ENOMEM;
+    c->desc = *d;
+    if (c->desc.kappa == 0.0) c->desc.kappa = 0.5;
+    auto bad = [&](const char *msg) {
+        c->err = msg;
+        *out = c;          // the caller can read the message, then destroy
+        return MLB_EINVAL;
+    };
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return bad("extents must be >= 1");
+    if (d->nspecies < 1 || d->nspecies > MLB_MAX_SPECIES) return bad("nspecies must be 1..4");
+    if (d->wall_axis < -1 || d->wall_axis > 2) return bad("wall_axis must be -1, 0, 1 or 2");
+    if (!(d->tau > 0.5) || !std::isfinite(d->tau)) return bad("tau must be finite and > 1/2");
+    if (!(std::fabs(d->kT - kCs2) < 1e-12)) return bad("kT must be 1/3 (D3Q19 lattice units)");
+    if (!(c->desc.kappa >= 0.0) || !std::isfinite(c->desc.kappa)) return bad("kappa must be >= 0");
+    if (d->flags & ~(MLB_DRAG_ONLY | MLB_FORCE_EXPLICIT)) return bad("unknown flag bits");
+    if (d->wall_axis >= 0) {
+        if (d->wall_u_lo[d->wall_axis] != 0.0 || d->wall_u_hi[d->wall_axis] != 0.0)
+            return bad("wall velocities must be tangential to the wall");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(d->wall_u_lo[k]) || !std::isfinite(d->wall_u_hi[k]) ||
+                std::fabs(d->wall_u_lo[k]) >= 0.5 || std::fabs(d->wall_u_hi[k]) >= 0.5)
+                return bad("wall velocities must be finite and below 0.5");
+    }
+    if ((bool)d->dev_alloc != (bool)d->dev_free) return bad("dev_alloc and dev_free must be given together");
+    const long long N = (long long)d->nx * d->ny * d->nz;
+    if (N > (1ll << 34)) return bad("lattice too large");
+    const int S = d->nspecies;
+
+    mlbi_params &p = c->p;
+    p.nx = d->nx; p.ny = d->ny; p.nz = d->nz; p.S = S; p.N = N;
+    p.wall_axis = d->wall_axis;
+    p.drag_only = (d->flags & MLB_DRAG_ONLY) ? 1 : 0;
+    p.semi_implicit = (d->flags & MLB_FORCE_EXPLICIT) ? 0 : 1;
+    p.omega = (float)(1.0 / d->tau);
+    p.src_scale = p.semi_implicit ? (float)(1.0 - 0.5 / d->tau) : 1.0f;
+    for (int k = 0; k < 3; ++k) {
+        p.wall_lo[k] = (float)d->wall_u_lo[k];
+        p.wall_hi[k] = (float)d->wall_u_hi[k];
+    }
+
+    if (d->stream) {
+        c->stream = (cudaStream_t)d->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            *out = c;
+            return MLB_ECUDA;
+        }
+        c->own_stream = true;
+    }
+
+    // one slab for every buffer
+    const int npairs = S * (S + 1) / 2;
+    size_t sz_f = align256(sizeof(float) * (size_t)S * MLBI_Q * N);
+    size_t sz_v4 = align256(sizeof(float4) * (size_t)S * N);
+    size_t sz_dg = align256(sizeof(float) * (size_t)npairs * N);
+    size_t sz_tab = align256(sizeof(mlbi_entry) * kTableCap);
+    size_t sz_stage = align256(sizeof(double) * (size_t)S * 4 * N);
+    size_t sz_part = align256(sizeof(double) * MLBI_RED_BLOCKS * (S + 3));
+    size_t sz_sums = align256(sizeof(double) * (S + 3));
+    size_t sz_flags = 256;
+    c->slab_bytes = 2 * sz_f + 4 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
+    if (d->dev_alloc) {
+        c->slab = d->dev_alloc(c->slab_bytes, d->alloc_user);
+        if (!c->slab) {
+            c->err = "dev_alloc returned NULL";
+            *out = c;
+            return MLB_ENOMEM;
+        }
+    } else {
+        cudaError_t e = cudaMalloc(&c->slab, c->slab_bytes);
+        if (e != cudaSuccess) {
+            c->slab = nullptr;
+            c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+            *out = c;
+            return MLB_ENOMEM;
+        }
+    }
+    char *q = (char *)c->slab;
+    c->b.f[0] = (float *)q; q += sz_f;
+    c->b.f[1] = (float *)q; q += sz_f;
+    c->b.mom = (float4 *)q; q += sz_v4;
+    c->b.frest = (float4 *)q; q += sz_v4;
+    c->b.du = (float4 *)q; q += sz_v4;
+    c->b.fext = (float4 *)q; q += sz_v4;
+    c->b.dg = (float *)q; q += sz_dg;
+    c->b.table = (const mlbi_entry *)q; q += sz_tab;
+    c->b.stage = (double *)q; q += sz_stage;
+    c->b.partial = (double *)q; q += sz_part;
+    c->b.sums = (double *)q; q += sz_sums;
+    c->b.flags = (unsigned int *)q;
+    cudaError_t e = cudaMemsetAsync(c->b.flags, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->b.fext, 0, sz_v4, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("initial memset: ") + cudaGetErrorString(e);
+        c->failed = true;
+        *out = c;
+        return MLB_ECUDA;
+    }
+    c->nref.assign(S, 0.0);
+    *out = c;
+    return MLB_OK;
+}
+
+mlb_status mlb_set_species(mlb_ctx *c, const double *sigma, const double *mass)
+{
+    MLB_GUARD(c);
+    if (!sigma || !mass) return fail(c, MLB_EINVAL, "sigma and mass are required");
+    const int S = c->desc.nspecies;
+    for (int a = 0; a < S; ++a) {
+        if (!std::isfinite(sigma[a]) || sigma[a] < 1.0 || sigma[a] > 64.0)
+            return fail(c, MLB_EINVAL, "sigma[%d] = %g must lie in [1, 64] lattice units", a, sigma[a]);
+        if (mass[a] != 1.0) return fail(c, MLB_EINVAL, "mass[%d] = %g: every mass must be 1", a, mass[a]);
+    }
+    std::vector<double> old_s = c->sigma, old_m = c->mass;
+    c->sigma.assign(sigma, sigma + S);
+    c->mass.assign(mass, mass + S);
+    if (c->eps.empty()) {
+        c->eps.assign(S * S, 0.0);
+        c->lambda_c.assign(S * S, 1.0);
+    }
+    mlb_status st = rebuild(c);
+    if (st != MLB_OK) {
+        c->sigma = old_s;
+        c->mass = old_m;
+        return st;
+    }
+    c->species_set = true;
+    return MLB_OK;
+}
+
+mlb_status mlb_set_interactions(mlb_ctx *c, const double *eps, const double *lambda_c)
+{
+    MLB_GUARD(c);
+    if (!c->species_set) return fail(c, MLB_ESTATE, "call mlb_set_species first");
+    const int S = c->desc.nspecies;
+    std::vector<double> e(S * S, 0.0), l(S * S, 1.0);
+    if (eps) {
+        if (!lambda_c) return fail(c, MLB_EINVAL, "lambda_c is required with eps");
+        for (int a = 0; a < S; ++a)
+            for (int b = 0; b < S; ++b) {
+                const double x = eps[a * S + b], y = lambda_c[a * S + b];
+                if (!std::isfinite(x) || x < 0.0 || x != eps[b * S + a])
+                    return fail(c, MLB_EINVAL, "eps must be finite, >= 0 and symmetric (entry %d,%d)", a, b);
+                if (!std::isfinite(y) || y < 1.0 || y > 16.0 || y != lambda_c[b * S + a])
+                    return fail(c, MLB_EINVAL, "lambda_c must be symmetric and in [1, 16] (entry %d,%d)", a, b);
+                e[a * S + b] = x;
+                l[a * S + b] = y;
+            }
+    }
+    std::vector<double> oe = c->eps, ol = c->lambda_c;
+    c->eps = e;
+    c->lambda_c = l;
+    mlb_status st = rebuild(c);
+    if (st != MLB_OK) {
+        c->eps = oe;
+        c->lambda_c = ol;
+        rebuild(c);
+    }
+    return st;
+}
+
+mlb_status mlb_set_fields(mlb_ctx *c, const double *n, const double *u)
+{
+    MLB_GUARD(c);
+    if (!c->species_set) return fail(c, MLB_ESTATE, "call mlb_set_species first");
+    if (!n) return fail(c, MLB_EINVAL, "n is required");
+    const int S = c->desc.nspecies;
+    const long long N = c->p.N;
+    std::vector<double> mean(S, 0.0);
+    for (int a = 0; a < S; ++a) {
+        double s = 0.0;
+        for (long long r = 0; r < N; ++r) {
+            const double v = n[a * N + r];
+            if (!std::isfinite(v) || v < 0.0) return fail(c, MLB_EINVAL, "n[%d][%lld] = %g is not a density", a, r, v);
+            s += v;
+        }
+        mean[a] = s / (double)N;
+    }
+    double v3[MLBI_MAXS];
+    for (int a = 0; a < S; ++a) v3[a] = kPi / 6.0 * c->sigma[a] * c->sigma[a] * c->sigma[a];
+    for (long long r = 0; r < N; ++r) {
+        double xi3 = 0.0;
+        for (int a = 0; a < S; ++a) xi3 += v3[a] * n[a * N + r];
+        if (!(xi3 < 1.0)) return fail(c, MLB_EINVAL, "packing xi3 = %g >= 1 at site %lld", xi3, r);
+    }
+    if (u)
+        for (long long k = 0; k < (long long)S * 3 * N; ++k)
+            if (!std::isfinite(u[k]) || std::fabs(u[k]) >= 1.0)
+                return fail(c, MLB_EINVAL, "velocity entry %lld = %g must be finite with |u| < 1", k, u[k]);
+    std::vector<double> old = c->nref;
+    for (int a = 0; a < S; ++a) c->nref[a] = (double)(float)mean[a];
+    mlb_status st = rebuild(c);
+    if (st != MLB_OK) {
+        c->nref = old;
+        return st;
+    }
+    double *dn = c->b.stage;
+    double *du = u ? c->b.stage + (size_t)S * N : nullptr;
+    MLB_CUDA(c, cudaMemcpyAsync(dn, n, sizeof(double) * S * N, cudaMemcpyHostToDevice, c->stream));
+    if (u) MLB_CUDA(c, cudaMemcpyAsync(du, u, sizeof(double) * S * 3 * N, cudaMemcpyHostToDevice, c->stream));
+    MLB_CUDA(c, mlbi_launch_init(c->p, c->b, c->cur, dn, du, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->fields_set = true;
+    c->step = 0;
+    return MLB_OK;
+}
+
+mlb_status mlb_set_external_force(mlb_ctx *c, const double *fext)
+{
+    MLB_GUARD(c);
+    const int S = c->desc.nspecies;
+    const long long N = c->p.N;
+    if (!fext) {
+        c->p.has_fext = 0;
+        return MLB_OK;
+    }
+    for (long long k = 0; k < (long long)S * 3 * N; ++k)
+        if (!std::isfinite(fext[k])) return fail(c, MLB_EINVAL, "fext entry %lld is not finite", k);
+    MLB_CUDA(c, cudaMemcpyAsync(c->b.stage, fext, sizeof(double) * S * 3 * N, cudaMemcpyHostToDevice, c->stream));
+    MLB_CUDA(c, mlbi_launch_import_fext(c->p, c->b, c->b.stage, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->p.has_fext = 1;
+    return MLB_OK;
+}
+
+mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    if (nsteps < 0) return fail(c, MLB_EINVAL, "nsteps must be >= 0");
+    for (int64_t t = 0; t < nsteps; ++t) {
+        st = forces(c);
+        if (st != MLB_OK) return st;
+        {
+            Timed tm(c, K_PASS2);
+            MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, c->b, c->cur, nullptr, c->stream));
+        }
+        c->cur ^= 1;
+        ++c->step;
+    }
+    return MLB_OK;
+}
+
+int32_t mlb_launches_per_step(const mlb_ctx *c)
+{
+    (void)c;
+    return K_NKINDS;
+}
+
+const char *mlb_kernel_name(int32_t k)
+{
+    return (k >= 0 && k < K_NKINDS) ? kKernelNames[k] : "";
+}
+
+mlb_status mlb_profile_enable(mlb_ctx *c, int32_t enable)
+{
+    MLB_GUARD(c);
+    c->profiling = enable != 0;
+    return MLB_OK;
+}
+
+int32_t mlb_profile_read(mlb_ctx *c, double *ms, int64_t *launches, int32_t max_kernels)
+{
+    if (!c || c->failed) return -1;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]) == cudaSuccess) {
+            c->prof_ms[c->ev_kind[k]] += t;
+            c->prof_count[c->ev_kind[k]] += 1;
+        }
+    }
+    c->ev_used = 0;
+    for (int k = 0; k < K_NKINDS && k < max_kernels; ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_count[k];
+        c->prof_ms[k] = 0.0;
+        c->prof_count[k] = 0;
+    }
+    return K_NKINDS;
+}
+
+mlb_status mlb_synchronize(mlb_ctx *c)
+{
+    MLB_GUARD(c);
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_flags(c);
+}
+
+mlb_status mlb_get_moments(mlb_ctx *c, double *n, double *u)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    const int S = c->desc.nspecies;
+    const long long N = c->p.N;
+    double *sn = c->b.stage, *su = c->b.stage + (size_t)S * N;
+    MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream));
+    MLB_CUDA(c, mlbi_launch_export_moments(c->p, c->b, sn, su, c->stream));
+    if (n) MLB_CUDA(c, cudaMemcpyAsync(n, sn, sizeof(double) * S * N, cudaMemcpyDeviceToHost, c->stream));
+    if (u) MLB_CUDA(c, cudaMemcpyAsync(u, su, sizeof(double) * S * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_flags(c);
+}
+
+mlb_status mlb_get_acceleration(mlb_ctx *c, double *acc)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    if (!acc) return fail(c, MLB_EINVAL, "acc is required");
+    const int S = c->desc.nspecies;
+    const long long N = c->p.N;
+    st = forces(c);
+    if (st != MLB_OK) return st;
+    MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, c->b, c->cur, c->b.stage, c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(acc, c->b.stage, sizeof(double) * S * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_flags(c);
+}
+
+mlb_status mlb_conservation(mlb_ctx *c, double *mass, double *mom)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    const int S = c->desc.nspecies;
+    double h[MLBI_MAXS + 3];
+    MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream));
+    MLB_CUDA(c, mlbi_launch_conservation(c->p, c->b, c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(h, c->b.sums, sizeof(double) * (S + 3), cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    st = check_flags(c);
+    if (st != MLB_OK) return st;
+    if (mass)
+        for (int a = 0; a < S; ++a) mass[a] = h[a];
+    if (mom)
+        for (int k = 0; k < 3; ++k) mom[k] = h[S + k];
+    return MLB_OK;
+}
+
+mlb_status mlb_get_populations(mlb_ctx *c, float *fdev, double *nref, int64_t *step)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    const int S = c->desc.nspecies;
+    const long long N = c->p.N;
+    if (fdev)
+        MLB_CUDA(c, cudaMemcpyAsync(fdev, c->b.f[c->cur], sizeof(float) * S * MLBI_Q * N, cudaMemcpyDeviceToHost,
+                                    c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (nref)
+        for (int a = 0; a < S; ++a) nref[a] = c->nref[a];
+    if (step) *step = c->step;
+    return MLB_OK;
+}
+
+mlb_status mlb_set_populations(mlb_ctx *c, const float *fdev, const double *nref, int64_t step)
+{
+    MLB_GUARD(c);
+    if (!c->species_set) return fail(c, MLB_ESTATE, "call mlb_set_species first");
+    if (!fdev || !nref) return fail(c, MLB_EINVAL, "fdev and nref are required");
+    const int S = c->desc.nspecies;
+    const long long N = c->p.N;
+    for (int a = 0; a < S; ++a)
+        if (!std::isfinite(nref[a]) || nref[a] < 0.0 || (double)(float)nref[a] != nref[a])
+            return fail(c, MLB_EINVAL, "nref[%d] must be a non-negative FP32-representable value", a);
+    for (long long k = 0; k < (long long)S * MLBI_Q * N; ++k)
+        if (!std::isfinite(fdev[k])) return fail(c, MLB_EINVAL, "population %lld is not finite", k);
+    std::vector<double> old = c->nref;
+    c->nref.assign(nref, nref + S);
+    mlb_status st = rebuild(c);
+    if (st != MLB_OK) {
+        c->nref = old;
+        return st;
+    }
+    MLB_CUDA(c, cudaMemcpyAsync(c->b.f[c->cur], fdev, sizeof(float) * S * MLBI_Q * N, cudaMemcpyHostToDevice,
+                                c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->fields_set = true;
+    c->step = step;
+    return MLB_OK;
+}
+
+const char *mlb_last_error(const mlb_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void mlb_destroy(mlb_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->slab) {
+        if (c->desc.dev_free) c->desc.dev_free(c->slab, c->desc.alloc_user);
+        else cudaFree(c->slab);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// mlb_internal.h -- definitions shared by the C-ABI runtime (mlb_api.cu) and
+// the sm_103a kernels (mlb_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MLBI_Q 19
+#define MLBI_MAXS 4
+#define MLBI_MAXP 10            // unordered species pairs for MLBI_MAXS species
+
+// One stencil entry: (x, y, z) = a unit vector s_d or a kernel vector, and
+// w = the offset d packed as three signed 10-bit fields (see mlbi_pack).
+typedef float4 mlbi_entry;
+
+__host__ __device__ inline int mlbi_pack(int dx, int dy, int dz)
+{
+    return (dx + 512) | ((dy + 512) << 10) | ((dz + 512) << 20);
+}
+__host__ __device__ inline void mlbi_unpack(int p, int &dx, int &dy, int &dz)
+{
+    dx = (p & 1023) - 512;
+    dy = ((p >> 10) & 1023) - 512;
+    dz = ((p >> 20) & 1023) - 512;
+}
+
+struct mlbi_pair {               // unordered pair a <= b
+    int shell_start, shell_count;    // half shell: one of each +-d
+    int attr_start, attr_count;      // half attraction region
+    float hc_pre;                    // kT sigma_ab^2 4 pi / |S_ab|
+    float vx_pre;                    // K_ab 4 pi / |S_ab|,  K_ab = 2 sigma_ab^2 sqrt(2 mu_ab kT / pi)
+    float h;                         // BMCSL h_ab = sigma_a sigma_b / (sigma_a + sigma_b)
+    float g_ref;                     // BMCSL contact value at the reference densities
+};
+
+struct mlbi_params {
+    int nx, ny, nz, S;
+    long long N;
+    int wall_axis;                   // -1 periodic
+    int drag_only;
+    int semi_implicit;               // 1: half-force shift, 0: forward Euler
+    int has_fext;
+    int has_attraction;
+    int npairs;
+    float omega;
+    float src_scale;                 // 1 - omega/2 (semi-implicit) or 1
+    float nref[MLBI_MAXS];
+    float xi2_coef[MLBI_MAXS];       // (pi/6) sigma^2
+    float xi3_coef[MLBI_MAXS];       // (pi/6) sigma^3
+    float xi2_ref, xi3_ref;
+    int ball_start[MLBI_MAXS], ball_count[MLBI_MAXS];
+    float ball_inv[MLBI_MAXS];
+    int pair_index[MLBI_MAXS][MLBI_MAXS];
+    mlbi_pair pair[MLBI_MAXP];
+    float wall_lo[3], wall_hi[3];
+};
+
+// Device buffers of one context (all carved from one allocation).
+struct mlbi_buffers {
+    float *f[2];                     // [S][19][N] populations minus w_i n_ref
+    float4 *mom;                     // [S][N]  (dn, jx, jy, jz), dn = n - n_ref
+    float *dg;                       // [npairs][N]  g_ab - g_ref_ab
+    float4 *frest;                   // [S][N]  hard core + attraction + external force
+    float4 *du;                      // [S][N]  half-step velocity shift from pass 1
+    float4 *fext;                    // [S][N]  external force (if any)
+    const mlbi_entry *table;         // stencil entries
+    double *stage;                   // [S*4*N] FP64 staging for host transfers
+    double *partial;                 // [MLBI_RED_BLOCKS][S+3] FP64 block sums
+    double *sums;                    // [S+3] final sums
+    unsigned int *flags;             // [1] numeric fault flags
+};
+
+#define MLBI_RED_BLOCKS 1024
+#define MLBI_FLAG_XI3 1u
+#define MLBI_FLAG_NAN 2u
+
+// kernel launchers (mlb_kernels.cu); each returns cudaGetLastError()
+cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
+cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
+cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
+cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, double *acc_out,
+                                      cudaStream_t s);
+cudaError_t mlbi_launch_init(const mlbi_params &p, const mlbi_buffers &b, int cur, const double *n,
+                             const double *u, cudaStream_t s);
+cudaError_t mlbi_launch_export_moments(const mlbi_params &p, const mlbi_buffers &b, double *n_out,
+                                       double *u_out, cudaStream_t s);
+cudaError_t mlbi_launch_import_fext(const mlbi_params &p, const mlbi_buffers &b, const double *fext,
+                                    cudaStream_t s);
+cudaError_t mlbi_launch_conservation(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of the C ABI in include/mlb.h (same names), plus a
+small convenience wrapper.  Argument marshalling only: every step of the
+method runs in the CUDA kernels of libmlb.so.  There is no fallback: if the
+library is missing or cannot load, importing raises.
+
+PyTorch supplies device memory (its caching allocator, through the
+``dev_alloc``/``dev_free`` callbacks) and the CUDA stream the context launches
+on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmlb.so")
+
+MLB_Q = 19
+MLB_MAX_SPECIES = 4
+MLB_DRAG_ONLY = 1
+MLB_FORCE_EXPLICIT = 2
+
+STATUS = {0: "MLB_OK", 1: "MLB_EINVAL", 2: "MLB_ENOMEM", 3: "MLB_ECUDA", 4: "MLB_ENUMERIC",
+          5: "MLB_ETIMEOUT", 6: "MLB_ESTATE"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class mlb_lattice_desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("nspecies", ctypes.c_int32), ("wall_axis", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("wall_u_lo", ctypes.c_double * 3), ("wall_u_hi", ctypes.c_double * 3),
+        ("tau", ctypes.c_double), ("kT", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class MLBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_1105_3634_gb300.build.build() "
+                          "(the CUDA library is required; there is no CPU path)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+    st = ctypes.c_int
+    L.mlb_create.argtypes = [ctypes.POINTER(mlb_lattice_desc), ctypes.POINTER(vp)]
+    L.mlb_create.restype = st
+    L.mlb_set_species.argtypes = [vp, dp, dp]
+    L.mlb_set_species.restype = st
+    L.mlb_set_interactions.argtypes = [vp, dp, dp]
+    L.mlb_set_interactions.restype = st
+    L.mlb_set_fields.argtypes = [vp, dp, dp]
+    L.mlb_set_fields.restype = st
+    L.mlb_set_external_force.argtypes = [vp, dp]
+    L.mlb_set_external_force.restype = st
+    L.mlb_step.argtypes = [vp, ctypes.c_int64]
+    L.mlb_step.restype = st
+    L.mlb_synchronize.argtypes = [vp]
+    L.mlb_synchronize.restype = st
+    L.mlb_get_moments.argtypes = [vp, dp, dp]
+    L.mlb_get_moments.restype = st
+    L.mlb_get_acceleration.argtypes = [vp, dp]
+    L.mlb_get_acceleration.restype = st
+    L.mlb_conservation.argtypes = [vp, dp, dp]
+    L.mlb_conservation.restype = st
+    L.mlb_get_populations.argtypes = [vp, fp, dp, ctypes.POINTER(ctypes.c_int64)]
+    L.mlb_get_populations.restype = st
+    L.mlb_set_populations.argtypes = [vp, fp, dp, ctypes.c_int64]
+    L.mlb_set_populations.restype = st
+    L.mlb_velocity_set.argtypes = [ctypes.POINTER(ctypes.c_int32), dp]
+    L.mlb_velocity_set.restype = st
+    L.mlb_launches_per_step.argtypes = [vp]
+    L.mlb_launches_per_step.restype = ctypes.c_int32
+    L.mlb_profile_enable.argtypes = [vp, ctypes.c_int32]
+    L.mlb_profile_enable.restype = st
+    L.mlb_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+    L.mlb_profile_read.restype = ctypes.c_int32
+    L.mlb_kernel_name.argtypes = [ctypes.c_int32]
+    L.mlb_kernel_name.restype = ctypes.c_char_p
+    L.mlb_last_error.argtypes = [vp]
+    L.mlb_last_error.restype = ctypes.c_char_p
+    L.mlb_status_string.argtypes = [ctypes.c_int]
+    L.mlb_status_string.restype = ctypes.c_char_p
+    L.mlb_destroy.argtypes = [vp]
+    L.mlb_destroy.restype = None
+    return L
+
+
+lib = _load()
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def velocity_set():
+    c = np.zeros((MLB_Q, 3), np.int32)
+    w = np.zeros(MLB_Q)
+    lib.mlb_velocity_set(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(w))
+    return c, w
+
+
+class _TorchAllocator:
+    """dev_alloc/dev_free callbacks backed by torch's caching allocator."""
+
+    def __init__(self, device: int, stream_ptr: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream_ptr = stream_ptr
+
+        def alloc(nbytes, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream_ptr or None))
+            except Exception:          # allocation failure -> NULL -> MLB_ENOMEM
+                return None
+
+        def free(ptr, user):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc_fn = ALLOC_FN(alloc)
+        self.free_fn = FREE_FN(free)
+
+
+class Simulation:
+    """One mlb context for a ``workloads.Lattice``.
+
+    stream: a torch.cuda.Stream (default: torch's current stream);
+    torch_alloc: take device memory from torch's caching allocator.
+    """
+
+    def __init__(self, lat, stream=None, torch_alloc: bool = True):
+        import torch
+        self.lat = lat
+        self.S = lat.nspecies
+        self.N = lat.nsites
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        d = mlb_lattice_desc()
+        d.nx, d.ny, d.nz = lat.shape
+        d.nspecies = self.S
+        d.wall_axis = lat.wall_axis
+        d.flags = (MLB_DRAG_ONLY if lat.drag_only else 0) | (
+            MLB_FORCE_EXPLICIT if lat.force_scheme == "explicit" else 0)
+        for k in range(3):
+            d.wall_u_lo[k] = lat.wall_u_lo[k]
+            d.wall_u_hi[k] = lat.wall_u_hi[k]
+        d.tau, d.kT, d.kappa = lat.tau, lat.kT, lat.kappa
+        d.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = _TorchAllocator(stream.device.index if stream.device.index is not None
+                                          else torch.cuda.current_device(), stream.cuda_stream)
+            d.dev_alloc = self._alloc.alloc_fn
+            d.dev_free = self._alloc.free_fn
+        self.ctx = ctypes.c_void_p()
+        st = lib.mlb_create(ctypes.byref(d), ctypes.byref(self.ctx))
+        self._check(st)
+        self._check(lib.mlb_set_species(self.ctx, _dp(np.ascontiguousarray(lat.sigma, np.float64)),
+                                        _dp(np.ascontiguousarray(lat.mass, np.float64))))
+        eps = np.ascontiguousarray(lat.eps, np.float64)
+        if np.any(eps != 0):
+            self._check(lib.mlb_set_interactions(self.ctx, _dp(eps),
+                                                 _dp(np.ascontiguousarray(lat.lambda_c, np.float64))))
+
+    # -- plumbing
+    def _check(self, st):
+        if st != 0:
+            msg = lib.mlb_last_error(self.ctx).decode() if self.ctx else ""
+            raise MLBError(st, msg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib.mlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the ABI, with numpy arrays
+    def set_fields(self, n, u=None):
+        n = np.ascontiguousarray(n, np.float64).reshape(self.S, self.N)
+        uu = None if u is None else np.ascontiguousarray(u, np.float64).reshape(self.S, 3, self.N)
+        self._check(lib.mlb_set_fields(self.ctx, _dp(n), _dp(uu)))
+
+    def set_external_force(self, fext):
+        fe = None if fext is None else np.ascontiguousarray(fext, np.float64).reshape(self.S, 3, self.N)
+        self._check(lib.mlb_set_external_force(self.ctx, _dp(fe)))
+
+    def step(self, nsteps: int):
+        self._check(lib.mlb_step(self.ctx, int(nsteps)))
+
+    def synchronize(self):
+        self._check(lib.mlb_synchronize(self.ctx))
+
+    def moments(self, out_n=None, out_u=None):
+        n = np.empty((self.S, self.N)) if out_n is None else out_n
+        u = np.empty((self.S, 3, self.N)) if out_u is None else out_u
+        self._check(lib.mlb_get_moments(self.ctx, _dp(n), _dp(u)))
+        return n, u
+
+    def acceleration(self):
+        a = np.empty((self.S, 3, self.N))
+        self._check(lib.mlb_get_acceleration(self.ctx, _dp(a)))
+        return a
+
+    def conservation(self):
+        m = np.empty(self.S)
+        p = np.empty(3)
+        self._check(lib.mlb_conservation(self.ctx, _dp(m), _dp(p)))
+        return m, p
+
+    def populations(self):
+        f = np.empty((self.S, MLB_Q, self.N), np.float32)
+        nref = np.empty(self.S)
+        step = ctypes.c_int64()
+        self._check(lib.mlb_get_populations(self.ctx, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            _dp(nref), ctypes.byref(step)))
+        return f, nref, step.value
+
+    def set_populations(self, f, nref, step=0):
+        f = np.ascontiguousarray(f, np.float32)
+        self._check(lib.mlb_set_populations(self.ctx, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            _dp(np.ascontiguousarray(nref, np.float64)), int(step)))
+
+    def launches_per_step(self) -> int:
+        return int(lib.mlb_launches_per_step(self.ctx))
+
+    def profile(self, enable: bool = True):
+        self._check(lib.mlb_profile_enable(self.ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since the last read."""
+        ms = np.zeros(8)
+        cnt = np.zeros(8, np.int64)
+        k = lib.mlb_profile_read(self.ctx, _dp(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 8)
+        if k < 0:
+            raise MLBError(6, "profile read failed")
+        return {lib.mlb_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}

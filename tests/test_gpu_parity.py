@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-wise comparison of densities, velocities and accelerations on the
+same seeded inputs.  Tolerance: 1e-5 on densities and velocities after 500
+steps (FP32 populations), measured normwise: max|x_gpu - x_oracle| divided
+by max|x_oracle| for the field x.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1105_3634_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_STATE = 1e-5      # densities, velocities (FP32 vs FP64)
+TOL_ACC = 1e-4        # accelerations from one FP32 force evaluation
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_3634_gb300 import build
+    build.build()
+    from paper_1105_3634_gb300 import mlb
+    return mlb
+
+
+U_FLOOR = 1e-9        # velocity scale below which a field counts as at rest
+
+
+def rel(a, b, floor=0.0):
+    """max|a - b| / max(max|b|, floor)."""
+    scale = max(float(np.abs(b).max()), floor)
+    return float(np.abs(a - b).max() / scale) if scale > 0 else float(np.abs(a - b).max())
+
+
+def run_pair(mlbmod, orc, lat, n, u=None, checkpoints=(0, 1, 50), fext=None, report=None):
+    """Advance GPU and oracle side by side; return the worst relative errors."""
+    sim = mlbmod.Simulation(lat)
+    sim.set_fields(n, u)
+    if fext is not None:
+        sim.set_external_force(fext)
+    f = orc.init(lat, n, u)
+    t = 0
+    worst = {"n": 0.0, "u": 0.0, "acc": 0.0}
+    for cp in checkpoints:
+        sim.step(cp - t)
+        orc.step(lat, f, cp - t, fext)
+        t = cp
+        gn, gu = sim.moments()
+        on, oj = orc.moments(lat, f)
+        ou = orc.velocity_fields(lat, on, oj)
+        e = {"n": rel(gn, on), "u": rel(gu, ou, U_FLOOR)}
+        ga = sim.acceleration()
+        oa = orc.accel(lat, on, oj, fext=fext)
+        e["acc"] = rel(ga, oa, U_FLOOR)
+        for k in worst:
+            worst[k] = max(worst[k], e[k])
+        if report is not None:
+            report.append((cp, e))
+    sim.close()
+    return worst
+
+
+def test_config1_500_steps(gpu, orc):
+    """Binary sigma = (1, 1.5), packing 0.2, tau = 1, 5% sine wave, 64x8x8, 500 steps."""
+    lat, n = W.binary_config1()
+    rep = []
+    w = run_pair(gpu, orc, lat, n, checkpoints=(0, 1, 10, 100, 500), report=rep)
+    print("config1", rep)
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
+
+
+def test_attraction_ragged_box(gpu, orc):
+    """sigma = (2, 3), eps = kT/2 tails cut at 2.5 sigma, packing 0.3, 1% noise,
+    on a ragged 18x16x17 box (every stencil wraps), 60 steps."""
+    lat, n = W.binary_attraction((18, 16, 17), seed=11)
+    rep = []
+    w = run_pair(gpu, orc, lat, n, checkpoints=(0, 1, 20, 60), report=rep)
+    print("attraction", rep)
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
+
+
+def test_taylor_channel_three_species_walls(gpu, orc):
+    """Two solvents sigma = 2, 2.5 and a dilute solute sigma = 3 between
+    walls moving at -U, +U (halfway bounce-back), 40x16x10, 150 steps."""
+    lat, n = W.taylor_channel((40, 16, 10), U=0.05)
+    n[2] = n[2] * 1e3 / 8            # a visible solute pulse on this small box
+    rep = []
+    w = run_pair(gpu, orc, lat, n, checkpoints=(0, 1, 30, 150), report=rep)
+    print("taylor", rep)
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
+
+
+@pytest.mark.parametrize("drag_only,scheme", [(True, "semi_implicit"), (False, "explicit"), (True, "explicit")])
+def test_flags_drag_only_and_forward_euler(gpu, orc, drag_only, scheme):
+    lat = W.Lattice(shape=(24, 9, 8), sigma=[1.0, 2.0], tau=0.8, drag_only=drag_only, force_scheme=scheme)
+    n0 = W.densities_from_packing(0.1, lat.sigma, [0.5, 0.5])
+    n = W.noise(lat, n0, 0.05, seed=4)
+    u = W.random_velocities(lat, 0.01, seed=9)
+    w = run_pair(gpu, orc, lat, n, u, checkpoints=(0, 1, 40))
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
+
+
+def test_external_force_and_initial_velocities(gpu, orc):
+    """A Kolmogorov-type body force F_x = F0 sin(2 pi y / L) on both species."""
+    lat = W.Lattice(shape=(10, 20, 9), sigma=[1.0, 1.5], tau=1.0)
+    n0 = W.densities_from_packing(0.15, lat.sigma, [0.5, 0.5])
+    n = W.noise(lat, n0, 0.02, seed=21)
+    y = W.coordinate(lat, 1)
+    fext = np.zeros((2, 3, lat.nsites))
+    fext[:, 0, :] = 1e-5 * np.sin(2 * math.pi * y / 20)[None, :]
+    u = W.random_velocities(lat, 0.005, seed=2)
+    w = run_pair(gpu, orc, lat, n, u, checkpoints=(0, 1, 80), fext=fext)
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
+
+
+def test_conservation_sums(gpu):
+    lat, n = W.binary_attraction((20, 18, 16), seed=5)
+    sim = gpu.Simulation(lat)
+    sim.set_fields(n, W.random_velocities(lat, 0.01, seed=1))
+    m0, p0 = sim.conservation()
+    assert np.allclose(m0, n.sum(1), rtol=1e-7)
+    sim.step(200)
+    m1, p1 = sim.conservation()
+    assert np.abs(m1 - m0).max() < 1e-6 * m0.max()
+    assert np.abs(p1 - p0).max() < 1e-6 * n.sum() * math.sqrt(1 / 3)
+    sim.close()
+
+
+def test_checkpoint_resume_is_bitwise(gpu):
+    lat, n = W.binary_attraction((16, 16, 16), seed=8)
+    sim = gpu.Simulation(lat)
+    sim.set_fields(n)
+    sim.step(20)
+    f20, nref, step = sim.populations()
+    assert step == 20
+    sim.step(15)
+    fa, _, _ = sim.populations()
+    sim2 = gpu.Simulation(lat)
+    sim2.set_populations(f20, nref, step)
+    sim2.step(15)
+    fb, _, stepb = sim2.populations()
+    assert stepb == 35
+    assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+    sim.close()
+    sim2.close()
+
+
+def test_zero_steps_and_rerun_determinism(gpu):
+    lat, n = W.binary_config1((32, 8, 8))
+    a = gpu.Simulation(lat)
+    a.set_fields(n)
+    f0, _, _ = a.populations()
+    a.step(0)
+    assert np.array_equal(a.populations()[0], f0)
+    a.step(7)
+    b = gpu.Simulation(lat)
+    b.set_fields(n)
+    b.step(7)
+    assert np.array_equal(a.populations()[0].view(np.uint32), b.populations()[0].view(np.uint32))
+
+
+def test_invalid_inputs_are_rejected(gpu):
+    lat, n = W.binary_config1((16, 8, 8))
+    sim = gpu.Simulation(lat)
+    with pytest.raises(gpu.MLBError, match="EINVAL"):
+        bad = n.copy(); bad[0, 3] = -1.0
+        sim.set_fields(bad)
+    with pytest.raises(gpu.MLBError, match="xi3"):
+        sim.set_fields(n * 10)
+    with pytest.raises(gpu.MLBError, match="ESTATE"):
+        sim.step(1)                     # no state yet
+    sim.set_fields(n)
+    sim.step(2)
+    with pytest.raises(gpu.MLBError, match="symmetric"):
+        sim._check(gpu.lib.mlb_set_interactions(sim.ctx, gpu._dp(np.array([[0.1, 0.2], [0.0, 0.1]])),
+                                                 gpu._dp(np.full((2, 2), 2.0))))
+    sim.close()
+    lat2 = W.Lattice(shape=(3, 8, 8), sigma=[2.0, 3.0])
+    with pytest.raises(gpu.MLBError, match="periodic extent"):
+        gpu.Simulation(lat2)
+    lat3 = W.Lattice(shape=(16, 16, 16), sigma=[1.0, 1.5], mass=[1.0, 2.0])
+    with pytest.raises(gpu.MLBError, match="mass"):
+        gpu.Simulation(lat3)
+
+
+def test_empty_species(gpu, orc):
+    """A species with zero density everywhere stays empty and exerts no force."""
+    lat = W.Lattice(shape=(16, 8, 8), sigma=[1.0, 1.5, 2.0])
+    n0 = W.densities_from_packing(0.15, lat.sigma[:2], [0.5, 0.5])
+    n = np.zeros((3, lat.nsites))
+    n[:2] = W.sine_wave(W.Lattice(shape=(16, 8, 8), sigma=[1.0, 1.5]), n0, 0.05)
+    w = run_pair(gpu, orc, lat, n, checkpoints=(0, 1, 30))
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
+
+
+def test_full_size_sampled(gpu, orc):
+    """256^3 binary (the benchmark workload, same launch sequence): after 3
+    steps the accelerations and the next populations at 48 sampled sites
+    equal the oracle's evaluated one by one from the GPU's own state."""
+    lat, n = W.binary_config1((256, 256, 256))
+    sim = gpu.Simulation(lat)
+    sim.set_fields(n)
+    sim.step(3)
+    gn, gu = sim.moments()
+    gj = gn[:, None, :] * gu
+    ga = sim.acceleration()
+    f_t, nref, _ = sim.populations()
+    sim.step(1)
+    f_t1, _, _ = sim.populations()
+    sim.close()
+    rng = np.random.default_rng(0)
+    N = lat.nsites
+    sites = np.sort(rng.choice(N, 48, replace=False))
+    sites[0] = 0                                  # a corner: every stencil wraps
+    g, _, _ = orc.gfield(lat, gn)
+    oa = orc.accel(lat, gn, gj, g=g, sites=sites)
+    assert rel(ga[:, :, sites], oa) < TOL_ACC
+    # populations at t+1 on the sampled sites: pull from the 19 source sites
+    cg, wg = gpu.velocity_set()
+    co, _ = orc.velocities()
+    perm = [int(np.where((co == v).all(1))[0][0]) for v in cg]        # gpu index -> oracle index
+    nx, ny, nz = lat.shape
+    x, y, z = sites % nx, (sites // nx) % ny, sites // (nx * ny)
+    src = np.stack([((x - cg[i, 0]) % nx) + nx * (((y - cg[i, 1]) % ny) + ny * ((z - cg[i, 2]) % nz))
+                    for i in range(19)], 1)                            # [M][19]
+    flat = src.reshape(-1)
+    oacc = orc.accel(lat, gn, gj, g=g, sites=flat)                    # [S][3][M*19]
+    ff = np.empty((flat.size, 2, 19))
+    for a in range(2):
+        for i in range(19):
+            ff[:, a, perm[i]] = f_t[a, i, flat].astype(np.float64) + wg[i] * nref[a]
+    post = orc.collide_local(lat, ff, gn[:, flat].T.copy(), np.transpose(gj[:, :, flat], (2, 0, 1)).copy(),
+                             np.transpose(oacc, (2, 0, 1)).copy())
+    post = post.reshape(len(sites), 19, 2, 19)
+    expect = np.empty((2, 19, len(sites)))
+    got = np.empty((2, 19, len(sites)))
+    for a in range(2):
+        for i in range(19):
+            expect[a, i] = post[:, i, a, perm[i]] - wg[i] * nref[a]
+            got[a, i] = f_t1[a, i, sites]
+    assert rel(got, expect) < TOL_STATE
