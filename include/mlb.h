@@ -157,6 +157,36 @@ mlb_status mlb_profile_enable(mlb_ctx *ctx, int32_t enable);
 int32_t mlb_profile_read(mlb_ctx *ctx, double *ms, int64_t *launches, int32_t max_kernels);
 const char *mlb_kernel_name(int32_t k);
 
+/* Conservation sums without any allocation (the paper has no counterpart:
+ * this serves callers that cannot let the library allocate).  A caller whose
+ * device memory is all owned by its own memory manager (a framework pool, a
+ * stream-ordered allocator that must not be mixed with cudaMalloc), or that
+ * must not allocate once a run is under way, cannot create a context, since
+ * mlb_create obtains all of a context's device memory.  This entry point
+ * computes the FP64 sums of mlb_conservation from populations the caller
+ * holds on the device, and allocates nothing: no cudaMalloc or cudaFree, no
+ * allocating library call.  Its reduction keeps its block partial sums in a
+ * fixed 28 KiB array (512 blocks x (MLB_MAX_SPECIES + 3) doubles) that every
+ * GPU which loads this library holds until the process exits.
+ *   fdev    device pointer, [nspecies][19][nsites] FP32 populations minus
+ *           w_i n_ref, in the mlb_velocity_set order (as mlb_get_populations
+ *           returns them); read only
+ *   nref    host array of nspecies reference densities
+ *   out     device pointer to nspecies + 3 doubles: mass[a] = sum_r n^a,
+ *           then sum_a sum_r j^a (masses 1); written by the call
+ *   stream  cudaStream_t the two kernels are launched on (asynchronous)
+ * Returns MLB_EINVAL for NULL pointers, nspecies outside 1..MLB_MAX_SPECIES
+ * (more species than the fixed array holds), nsites outside 1..2^34 or a
+ * non-finite nref; MLB_ECUDA if the lookup or a launch fails (no context, so
+ * no message).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents: every call overwrites each partial it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller. */
+mlb_status mlb_conservation_noalloc(const float *fdev, const double *nref, int32_t nspecies, int64_t nsites,
+                                    double *out, void *stream);
+
 const char *mlb_last_error(const mlb_ctx *ctx);
 const char *mlb_status_string(mlb_status s);
 void mlb_destroy(mlb_ctx *ctx);

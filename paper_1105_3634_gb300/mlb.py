@@ -88,6 +88,8 @@ def _load():
     L.mlb_profile_read.restype = ctypes.c_int32
     L.mlb_kernel_name.argtypes = [ctypes.c_int32]
     L.mlb_kernel_name.restype = ctypes.c_char_p
+    L.mlb_conservation_noalloc.argtypes = [vp, dp, ctypes.c_int32, ctypes.c_int64, vp, vp]
+    L.mlb_conservation_noalloc.restype = st
     L.mlb_last_error.argtypes = [vp]
     L.mlb_last_error.restype = ctypes.c_char_p
     L.mlb_status_string.argtypes = [ctypes.c_int]
