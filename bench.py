@@ -61,15 +61,18 @@ def config_dict(size):
 
 
 # ------------------------------------------------------------------ per-kernel algorithmic bytes
-def algorithmic_bytes(kernel, S, npairs, has_fext=False):
-    """Bytes per species-site that the kernel must move by design."""
+def algorithmic_bytes(kernel, S, npairs, has_fext=False, local_g=True):
+    """Bytes per species-site that the kernel must move by design (FP32)."""
     g = 4.0 * npairs / S
-    return {
-        "k_moments": 76 + 16,                                  # f read, (dn, j) write
-        "k_gfield": 4 + g,                                     # dn read, g write
-        "k_pass1": 16 + g + 12 + 12 + (12 if has_fext else 0),  # moments, g read; frest, du write
-        "k_pass2_collide": 76 + 16 + g + 12 + 12 + 76,         # f, moments, g, frest, du read; f write
-    }[kernel]
+    table = {
+        # f read, (dn, j) write (+ g write when the contact values are site-local)
+        "k_moments": 76 + 16 + (g if local_g else 0),
+        "k_gfield": 4 + g,                                       # dn read, g write
+        "k_pass1": 16 + g + 12 + 16 + (12 if has_fext else 0),    # moments, g read; frest, p* write
+        "k_pass2": 16 + g + 12 + 16 + 12,                          # moments, g, frest, p* read; acc write
+        "k_collide": 76 + 16 + 12 + 76,                            # f, moments, acc read; f write
+    }
+    return table.get(kernel)
 
 
 def measured_peak_hbm():
@@ -237,11 +240,13 @@ def run_mlb(args, rank, world, local_rank):
         if cnt == 0:
             continue
         per_launch_ms = ms / cnt
-        b = algorithmic_bytes(name, S, npairs) * S * N
+        bss = algorithmic_bytes(name, S, npairs)
+        b = bss * S * N if bss is not None else None
         kernels[name] = {"launches": cnt, "ms_total": ms, "ms_per_launch": per_launch_ms,
                          "share": ms / sum(v[0] for v in prof.values()),
-                         "algorithmic_bytes_per_launch": b, "achieved_gbs": b / (per_launch_ms * 1e-3) / 1e9}
-    top = max(kernels, key=lambda k: kernels[k]["ms_total"])
+                         "algorithmic_bytes_per_launch": b,
+                         "achieved_gbs": (b / (per_launch_ms * 1e-3) / 1e9) if b is not None else None}
+    top = max((k for k in kernels if kernels[k]["achieved_gbs"] is not None), key=lambda k: kernels[k]["ms_total"])
     roof = {"kernel": top, "bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak,
             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "unit": "GB/s", "frac": kernels[top]["achieved_gbs"] / peak, "traffic": None}

@@ -16,7 +16,7 @@
 
 namespace {
 
-constexpr int kTableCap = 16384;               // stencil entries per context (256 KiB)
+constexpr int kTableCap = 16384;               // stencil entries per context (2 float4 each, 512 KiB)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kCs2 = 1.0 / 3.0;
 
@@ -98,29 +98,53 @@ bool canonical(int dx, int dy, int dz)
 mlb_status rebuild(mlb_ctx *c)
 {
     const int S = c->desc.nspecies;
+    const long long nx = c->desc.nx, nxy = (long long)c->desc.nx * c->desc.ny;
     mlbi_params &p = c->p;
     std::vector<mlbi_entry> tab;
     int maxoff = 1;
-    auto push = [&](int dx, int dy, int dz, double vx, double vy, double vz) {
-        mlbi_entry e;
-        e.x = (float)vx; e.y = (float)vy; e.z = (float)vz;
+    bool lin_overflow = false;
+    // reach of the union shells: the tiled kernels stage a halo of this width
+    int shell_reach = 1;
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            const double sab = 0.5 * (c->sigma[a] + c->sigma[b]);
+            shell_reach = std::max(shell_reach, (int)std::floor(std::sqrt(std::pow(sab + 0.5, 2) - 1e-9)));
+        }
+    const int tile_r = shell_reach <= 2 ? shell_reach : 0;
+    const int txh = 32 + 2 * tile_r;
+    auto push = [&](int dx, int dy, int dz, double vx, double vy, double vz, int mask) {
+        mlbi_entry e0, e1;
+        e0.x = (float)vx; e0.y = (float)vy; e0.z = (float)vz;
         int packed = mlbi_pack(dx, dy, dz);
-        std::memcpy(&e.w, &packed, sizeof(int));
-        tab.push_back(e);
+        std::memcpy(&e0.w, &packed, sizeof(int));
+        long long lin = dx + nx * dy + nxy * dz;
+        if (lin >= (1ll << 31) || lin <= -(1ll << 31)) lin_overflow = true;
+        int lin32 = (int)lin, tileoff = dx + txh * dy, dzz = dz;
+        std::memcpy(&e1.x, &lin32, sizeof(int));
+        std::memcpy(&e1.y, &mask, sizeof(int));
+        std::memcpy(&e1.z, &tileoff, sizeof(int));
+        std::memcpy(&e1.w, &dzz, sizeof(int));
+        tab.push_back(e0);
+        tab.push_back(e1);
         maxoff = std::max(maxoff, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
     };
+    auto count = [&]() { return (int)(tab.size() / 2); };
     // smoothing balls |d| <= kappa sigma_c (origin included)
     for (int g = 0; g < S; ++g) {
         double R = c->desc.kappa * c->sigma[g];
         int Ri = (int)std::floor(R) + 1;
-        p.ball_start[g] = (int)tab.size();
+        p.ball_start[g] = count();
         for (int dz = -Ri; dz <= Ri; ++dz)
             for (int dy = -Ri; dy <= Ri; ++dy)
                 for (int dx = -Ri; dx <= Ri; ++dx)
-                    if ((double)(dx * dx + dy * dy + dz * dz) <= R * R) push(dx, dy, dz, 0, 0, 0);
-        p.ball_count[g] = (int)tab.size() - p.ball_start[g];
+                    if ((double)(dx * dx + dy * dy + dz * dz) <= R * R) push(dx, dy, dz, 0, 0, 0, 0);
+        p.ball_count[g] = count() - p.ball_start[g];
         p.ball_inv[g] = 1.0f / (float)p.ball_count[g];
     }
+    auto in_shell = [](double sab, int dx, int dy, int dz) {
+        const double q = (double)(dx * dx + dy * dy + dz * dz), lo = sab - 0.5, hi = sab + 0.5;
+        return q > 0.0 && q >= (lo > 0 ? lo * lo : 0.0) && q < hi * hi;
+    };
     // pairs
     int np = 0;
     bool attraction = false;
@@ -133,19 +157,16 @@ mlb_status rebuild(mlb_ctx *c)
         for (int b = a; b < S; ++b) {
             mlbi_pair &pr = p.pair[np];
             const double sab = 0.5 * (c->sigma[a] + c->sigma[b]);
-            const double lo = sab - 0.5, hi = sab + 0.5;
-            const int Ri = (int)std::ceil(hi) + 1;
-            pr.shell_start = (int)tab.size();
+            const int Ri = (int)std::ceil(sab + 0.5) + 1;
+            pr.shell_start = count();
             for (int dz = -Ri; dz <= Ri; ++dz)
                 for (int dy = -Ri; dy <= Ri; ++dy)
                     for (int dx = -Ri; dx <= Ri; ++dx) {
-                        const double q = (double)(dx * dx + dy * dy + dz * dz);
-                        if (q == 0.0 || !canonical(dx, dy, dz)) continue;
-                        if (q < (lo > 0 ? lo * lo : 0.0) || !(q < hi * hi)) continue;
-                        const double len = std::sqrt(q);
-                        push(dx, dy, dz, dx / len, dy / len, dz / len);
+                        if (!canonical(dx, dy, dz) || !in_shell(sab, dx, dy, dz)) continue;
+                        const double len = std::sqrt((double)(dx * dx + dy * dy + dz * dz));
+                        push(dx, dy, dz, dx / len, dy / len, dz / len, 0);
                     }
-            pr.shell_count = (int)tab.size() - pr.shell_start;
+            pr.shell_count = count() - pr.shell_start;
             const double wS = 4.0 * kPi / (2.0 * pr.shell_count);
             const double mu = c->mass[a] * c->mass[b] / (c->mass[a] + c->mass[b]);
             pr.hc_pre = (float)(c->desc.kT * sab * sab * wS);
@@ -153,7 +174,7 @@ mlb_status rebuild(mlb_ctx *c)
             pr.h = (float)(c->sigma[a] * c->sigma[b] / (c->sigma[a] + c->sigma[b]));
             pr.g_ref = (float)bmcsl(c->sigma[a], c->sigma[b], xi2, xi3);
             // attraction: K(d) = 6 eps sigma^6 d / |d|^8 on sigma <= |d| <= lambda_c sigma
-            pr.attr_start = (int)tab.size();
+            pr.attr_start = count();
             const double e = c->eps.empty() ? 0.0 : c->eps[a * S + b];
             if (e != 0.0) {
                 attraction = true;
@@ -167,16 +188,36 @@ mlb_status rebuild(mlb_ctx *c)
                             if (q == 0.0 || !canonical(dx, dy, dz)) continue;
                             if (q < sab * sab || q > rc * rc) continue;
                             const double k = 6.0 * e * s6 / (q * q * q * q);
-                            push(dx, dy, dz, k * dx, k * dy, k * dz);
+                            push(dx, dy, dz, k * dx, k * dy, k * dz, 0);
                         }
             }
-            pr.attr_count = (int)tab.size() - pr.attr_start;
+            pr.attr_count = count() - pr.attr_start;
             p.pair_index[a][b] = p.pair_index[b][a] = np;
             ++np;
         }
-    if ((int)tab.size() > kTableCap)
-        return fail(c, MLB_EINVAL, "stencil tables need %zu entries, capacity is %d (reduce sigma or lambda_c)",
-                    tab.size(), kTableCap);
+    // union half shells per neighbour species b, with a mask of the species a
+    // whose pair shell (a, b) contains the offset
+    for (int b = 0; b < S; ++b) {
+        int R = 1;
+        for (int a = 0; a < S; ++a) R = std::max(R, (int)std::ceil(0.5 * (c->sigma[a] + c->sigma[b]) + 0.5) + 1);
+        p.ushell_start[b] = count();
+        for (int dz = -R; dz <= R; ++dz)
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dx = -R; dx <= R; ++dx) {
+                    if (!canonical(dx, dy, dz)) continue;
+                    int mask = 0;
+                    for (int a = 0; a < S; ++a)
+                        if (in_shell(0.5 * (c->sigma[a] + c->sigma[b]), dx, dy, dz)) mask |= 1 << a;
+                    if (!mask) continue;
+                    const double len = std::sqrt((double)(dx * dx + dy * dy + dz * dz));
+                    push(dx, dy, dz, dx / len, dy / len, dz / len, mask);
+                }
+        p.ushell_count[b] = count() - p.ushell_start[b];
+    }
+    if (lin_overflow) return fail(c, MLB_EINVAL, "stencil offsets exceed 32-bit linear offsets on this lattice");
+    if (count() > kTableCap)
+        return fail(c, MLB_EINVAL, "stencil tables need %d entries, capacity is %d (reduce sigma or lambda_c)",
+                    count(), kTableCap);
     const int L[3] = {c->desc.nx, c->desc.ny, c->desc.nz};
     for (int ax = 0; ax < 3; ++ax)
         if (ax != c->desc.wall_axis && L[ax] <= maxoff)
@@ -185,6 +226,12 @@ mlb_status rebuild(mlb_ctx *c)
                         maxoff);
     p.npairs = np;
     p.has_attraction = attraction ? 1 : 0;
+    p.local_g = 1;
+    for (int g = 0; g < S; ++g)
+        if (p.ball_count[g] != 1) p.local_g = 0;
+    p.tile_r = tile_r;
+    p.zchunk = std::min(c->desc.nz, 16);
+    p.reach = maxoff;
     p.xi2_ref = (float)xi2;
     p.xi3_ref = (float)xi3;
     for (int g = 0; g < S; ++g) {
@@ -217,8 +264,8 @@ mlb_status require_ready(mlb_ctx *c)
     return MLB_OK;
 }
 
-enum { K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_NKINDS = 4 };
-const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2_collide"};
+enum { K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_NKINDS = 5 };
+const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2", "k_collide"};
 
 // event pair around one launch when profiling
 struct Timed {
@@ -248,9 +295,15 @@ struct Timed {
 // The force passes of one step on the current populations.
 mlb_status forces(mlb_ctx *c)
 {
-    { Timed t(c, K_MOMENTS); MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream)); }
-    { Timed t(c, K_GFIELD); MLB_CUDA(c, mlbi_launch_gfield(c->p, c->b, c->stream)); }
+    if (c->p.local_g) {
+        Timed t(c, K_MOMENTS);
+        MLB_CUDA(c, mlbi_launch_moments_g(c->p, c->b, c->cur, c->stream));
+    } else {
+        { Timed t(c, K_MOMENTS); MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream)); }
+        { Timed t(c, K_GFIELD); MLB_CUDA(c, mlbi_launch_gfield(c->p, c->b, c->stream)); }
+    }
     { Timed t(c, K_PASS1); MLB_CUDA(c, mlbi_launch_pass1(c->p, c->b, c->stream)); }
+    { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
     return MLB_OK;
 }
 
@@ -317,6 +370,8 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     if ((bool)d->dev_alloc != (bool)d->dev_free) return bad("dev_alloc and dev_free must be given together");
     const long long N = (long long)d->nx * d->ny * d->nz;
     if (N > (1ll << 34)) return bad("lattice too large");
+    if (d->nz > 65535 || d->ny > 65535 * 4) return bad("ny must be <= 262140 and nz <= 65535");
+    if ((long long)d->nx * d->ny >= (1ll << 30)) return bad("nx * ny must be below 2^30");
     const int S = d->nspecies;
 
     mlbi_params &p = c->p;
@@ -348,12 +403,12 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     size_t sz_f = align256(sizeof(float) * (size_t)S * MLBI_Q * N);
     size_t sz_v4 = align256(sizeof(float4) * (size_t)S * N);
     size_t sz_dg = align256(sizeof(float) * (size_t)npairs * N);
-    size_t sz_tab = align256(sizeof(mlbi_entry) * kTableCap);
+    size_t sz_tab = align256(sizeof(mlbi_entry) * 2 * kTableCap);
     size_t sz_stage = align256(sizeof(double) * (size_t)S * 4 * N);
     size_t sz_part = align256(sizeof(double) * MLBI_RED_BLOCKS * (S + 3));
     size_t sz_sums = align256(sizeof(double) * (S + 3));
     size_t sz_flags = 256;
-    c->slab_bytes = 2 * sz_f + 4 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
+    c->slab_bytes = 2 * sz_f + 6 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
     if (d->dev_alloc) {
         c->slab = d->dev_alloc(c->slab_bytes, d->alloc_user);
         if (!c->slab) {
@@ -375,7 +430,9 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     c->b.f[1] = (float *)q; q += sz_f;
     c->b.mom = (float4 *)q; q += sz_v4;
     c->b.frest = (float4 *)q; q += sz_v4;
+    c->b.pst = (float4 *)q; q += sz_v4;
     c->b.du = (float4 *)q; q += sz_v4;
+    c->b.acc = (float4 *)q; q += sz_v4;
     c->b.fext = (float4 *)q; q += sz_v4;
     c->b.dg = (float *)q; q += sz_dg;
     c->b.table = (const mlbi_entry *)q; q += sz_tab;
@@ -529,8 +586,8 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
         st = forces(c);
         if (st != MLB_OK) return st;
         {
-            Timed tm(c, K_PASS2);
-            MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, c->b, c->cur, nullptr, c->stream));
+            Timed tm(c, K_COLLIDE);
+            MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream));
         }
         c->cur ^= 1;
         ++c->step;
@@ -540,8 +597,7 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
-    (void)c;
-    return K_NKINDS;
+    return (c && c->p.local_g) ? K_NKINDS - 1 : K_NKINDS;
 }
 
 const char *mlb_kernel_name(int32_t k)
@@ -610,7 +666,7 @@ mlb_status mlb_get_acceleration(mlb_ctx *c, double *acc)
     const long long N = c->p.N;
     st = forces(c);
     if (st != MLB_OK) return st;
-    MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, c->b, c->cur, c->b.stage, c->stream));
+    MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, c->b.stage, c->stream));
     MLB_CUDA(c, cudaMemcpyAsync(acc, c->b.stage, sizeof(double) * S * 3 * N, cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     return check_flags(c);

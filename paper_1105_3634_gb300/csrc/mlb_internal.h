@@ -9,8 +9,14 @@
 #define MLBI_MAXS 4
 #define MLBI_MAXP 10            // unordered species pairs for MLBI_MAXS species
 
-// One stencil entry: (x, y, z) = a unit vector s_d or a kernel vector, and
-// w = the offset d packed as three signed 10-bit fields (see mlbi_pack).
+// One stencil entry is two float4 in the table:
+//   e0 = (x, y, z, packed d): a unit vector s_d or a kernel vector, and the
+//        offset d packed as three signed 10-bit fields (see mlbi_pack);
+//   e1 = (linear offset of d for this lattice, mask, tile offset, dz) as
+//        int bits; the mask (union shells) has bit a set when d lies in the
+//        shell of the pair (a, b) of the table's neighbour species b; the
+//        tile offset dx + dy (32 + 2 tile_r) addresses d inside a plane of
+//        the shared-memory tile of the tiled kernels.
 typedef float4 mlbi_entry;
 
 __host__ __device__ inline int mlbi_pack(int dx, int dy, int dz)
@@ -24,9 +30,9 @@ __host__ __device__ inline void mlbi_unpack(int p, int &dx, int &dy, int &dz)
     dz = ((p >> 20) & 1023) - 512;
 }
 
-struct mlbi_pair {               // unordered pair a <= b
-    int shell_start, shell_count;    // half shell: one of each +-d
-    int attr_start, attr_count;      // half attraction region
+struct mlbi_pair {               // unordered pair a <= b, index a*S - a(a-1)/2 + (b - a)
+    int shell_start, shell_count;    // half shell: one of each +-d (entries)
+    int attr_start, attr_count;      // half attraction region (entries)
     float hc_pre;                    // kT sigma_ab^2 4 pi / |S_ab|
     float vx_pre;                    // K_ab 4 pi / |S_ab|,  K_ab = 2 sigma_ab^2 sqrt(2 mu_ab kT / pi)
     float h;                         // BMCSL h_ab = sigma_a sigma_b / (sigma_a + sigma_b)
@@ -50,6 +56,11 @@ struct mlbi_params {
     float xi2_ref, xi3_ref;
     int ball_start[MLBI_MAXS], ball_count[MLBI_MAXS];
     float ball_inv[MLBI_MAXS];
+    int ushell_start[MLBI_MAXS], ushell_count[MLBI_MAXS];   // union half shells per neighbour species
+    int reach;                       // largest offset component of any stencil (>= 1)
+    int local_g;                     // every smoothing ball is the single site
+    int tile_r;                      // reach of the union shells if the tiled kernels serve it (1, 2), else 0
+    int zchunk;                      // planes per block of the tiled kernels
     int pair_index[MLBI_MAXS][MLBI_MAXS];
     mlbi_pair pair[MLBI_MAXP];
     float wall_lo[3], wall_hi[3];
@@ -60,8 +71,10 @@ struct mlbi_buffers {
     float *f[2];                     // [S][19][N] populations minus w_i n_ref
     float4 *mom;                     // [S][N]  (dn, jx, jy, jz), dn = n - n_ref
     float *dg;                       // [npairs][N]  g_ab - g_ref_ab
-    float4 *frest;                   // [S][N]  hard core + attraction + external force
-    float4 *du;                      // [S][N]  half-step velocity shift from pass 1
+    float4 *frest;                   // [S][N]  pass 1 -> 2: F^hc + G + F_ext - Gamma du
+    float4 *pst;                     // [S][N]  pass 1 -> 2: (n - n_ref, j + n du)
+    float4 *du;                      // [S][N]  pass 1 -> 2: du (drag-only mode)
+    float4 *acc;                     // [S][N]  pass 2 -> collide: acceleration
     float4 *fext;                    // [S][N]  external force (if any)
     const mlbi_entry *table;         // stencil entries
     double *stage;                   // [S*4*N] FP64 staging for host transfers
@@ -78,8 +91,9 @@ struct mlbi_buffers {
 cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
-cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, double *acc_out,
-                                      cudaStream_t s);
+cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
+cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s);
+cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_init(const mlbi_params &p, const mlbi_buffers &b, int cur, const double *n,
                              const double *u, cudaStream_t s);
 cudaError_t mlbi_launch_export_moments(const mlbi_params &p, const mlbi_buffers &b, double *n_out,

@@ -5,18 +5,20 @@
 //   f[a][i][r]  FP32 populations minus w_i n_ref^a      (76 B per species-site)
 //   mom[a][r]   float4 (n - n_ref, j_x, j_y, j_z)        (16 B per species-site)
 //   dg[p][r]    g_ab - g_ab(reference densities)          (per unordered pair)
-//   frest[a][r] hard core + attraction + external force  (pass 1 -> pass 2)
-//   du[a][r]    half-step velocity shift of pass 1       (pass 1 -> pass 2)
+//   frest[a][r] F^hc + G + F_ext - Gamma du               (pass 1 -> pass 2)
+//   pst[a][r]   (n - n_ref, j + n du)                     (pass 1 -> pass 2)
 //
 // One step (all launches on one stream):
 //   k_moments        f -> mom                                    (Eq. colonna)
 //   k_gfield         mom -> dg: smoothed densities, BMCSL g       (Sec. II smoothing)
-//   k_pass1          mom, dg -> frest, du                         (Eqs. potmeanforce, gammaab,
-//                    hard core + attraction + velocity exchange    viscousforce)
-//                    at u, then the one-sweep half-step predictor
-//   k_pass2_collide  velocity exchange at u + du, collision toward (Eqs. evolution, prefactor)
-//                    psi_perp at u + a/2 with (1 - omega/2) forcing,
-//                    push-streaming / halfway bounce-back
+//   (k_moments_g     the two above in one pass when g is site-local)
+//   k_pass1          mom, dg -> frest, pst: hard core + attraction  (Eqs. potmeanforce, gammaab,
+//                    + velocity exchange at u, then the one-sweep    viscousforce)
+//                    half-step predictor
+//   k_pass2          velocity exchange at u + du -> acc
+//   k_collide        collision toward psi_perp at u + a/2 with      (Eqs. evolution, prefactor)
+//                    (1 - omega/2) forcing, push streaming /
+//                    halfway bounce-back
 // Deviations from reference values (n - n_ref, g - g_ref) keep the FP32
 // differences that the contact sums take small and exact where they cancel.
 #include "mlb_internal.h"
@@ -36,15 +38,26 @@ __device__ constexpr float WQ[MLBI_Q] = {1.f / 3.f,
 
 __device__ __forceinline__ int opposite(int i) { return i == 0 ? 0 : (((i - 1) ^ 1) + 1); }
 
+// the same velocity set for a runtime index, from bit tables (no memory access):
+// component = (bit of "plus" mask) - (bit of "minus" mask)
+__device__ __forceinline__ int comp_of(int i, unsigned plus, unsigned minus)
+{
+    return (int)((plus >> i) & 1u) - (int)((minus >> i) & 1u);
+}
+__device__ __forceinline__ int CXv(int i) { return comp_of(i, 0x2A82u, 0x5504u); }
+__device__ __forceinline__ int CYv(int i) { return comp_of(i, 0x28488u, 0x50310u); }
+__device__ __forceinline__ int CZv(int i) { return comp_of(i, 0x4C820u, 0x33040u); }
+__device__ __forceinline__ float WQv(int i) { return i == 0 ? 1.f / 3.f : (i < 7 ? 1.f / 18.f : 1.f / 36.f); }
+
 constexpr int kBlock = 256;
 constexpr float kTinyDensity = 1e-12f;
 
-__device__ __forceinline__ void site_coords(const mlbi_params &p, long long r, int &x, int &y, int &z)
+inline unsigned grid_for(long long N)
 {
-    x = (int)(r % p.nx);
-    long long t = r / p.nx;
-    y = (int)(t % p.ny);
-    z = (int)(t / p.ny);
+    long long g = (N + kBlock - 1) / kBlock;
+    if (g < 1) g = 1;
+    if (g > (1ll << 30)) g = 1ll << 30;
+    return (unsigned)g;
 }
 
 // r + d with periodic wrap (|d| < extent is guaranteed by the host) or -1 beyond a wall
@@ -58,33 +71,6 @@ __device__ __forceinline__ long long neighbour(const mlbi_params &p, int x, int 
     if (p.wall_axis == 2) { if (c2 < 0 || c2 >= p.nz) return -1; }
     else { c2 += (c2 < 0) ? p.nz : 0; c2 -= (c2 >= p.nz) ? p.nz : 0; }
     return c0 + (long long)p.nx * (c1 + (long long)p.ny * c2);
-}
-
-struct SiteState {                 // moments of every species at one site
-    float n[MLBI_MAXS];            // full density
-    float dn[MLBI_MAXS];           // n - n_ref
-    float u[MLBI_MAXS][3];         // species velocity (barycentric where n is tiny)
-    float j[MLBI_MAXS][3];
-};
-
-__device__ __forceinline__ void load_site(const mlbi_params &p, const float4 *__restrict__ mom, long long r,
-                                          SiteState &s)
-{
-    float rho = 0.f, m[3] = {0.f, 0.f, 0.f};
-    for (int a = 0; a < p.S; ++a) {
-        float4 v = mom[a * p.N + r];
-        s.dn[a] = v.x;
-        s.n[a] = p.nref[a] + v.x;
-        s.j[a][0] = v.y; s.j[a][1] = v.z; s.j[a][2] = v.w;
-        rho += s.n[a];
-        m[0] += v.y; m[1] += v.z; m[2] += v.w;
-    }
-    float inv = rho > 0.f ? 1.f / rho : 0.f;
-    for (int a = 0; a < p.S; ++a) {
-        bool ok = s.n[a] > kTinyDensity;
-        float in = ok ? 1.f / s.n[a] : 0.f;
-        for (int k = 0; k < 3; ++k) s.u[a][k] = ok ? s.j[a][k] * in : m[k] * inv;
-    }
 }
 
 // ------------------------------------------------------------------ moments
@@ -110,6 +96,47 @@ __global__ void __launch_bounds__(kBlock) k_moments(mlbi_params p, const float *
     }
 }
 
+// ------------------------------------------------------------------ site mapping of the stencil kernels
+// Blocks of 32 x 4 sites (x fastest): a warp covers 32 consecutive x, so
+// every stream of the structure of arrays is read in 128-byte rows.  Sites
+// farther than `reach` from every face (the interior) address neighbours by
+// the precomputed linear offset of each stencil entry; the others wrap or
+// stop at walls through `neighbour`.
+constexpr int kBX = 32, kBY = 4;
+
+struct Loc {
+    int x, y, z;
+    long long r;
+    bool interior;
+};
+
+__device__ __forceinline__ bool locate(const mlbi_params &p, Loc &L)
+{
+    L.x = blockIdx.x * kBX + threadIdx.x;
+    L.y = blockIdx.y * kBY + threadIdx.y;
+    L.z = blockIdx.z;
+    if (L.x >= p.nx || L.y >= p.ny) return false;
+    L.r = L.x + (long long)p.nx * (L.y + (long long)p.ny * L.z);
+    const int R = p.reach;
+    L.interior = L.x >= R && L.x < p.nx - R && L.y >= R && L.y < p.ny - R && L.z >= R && L.z < p.nz - R;
+    return true;
+}
+
+// index of r + sign*d for table entry (e0, e1), or -1 beyond a wall
+__device__ __forceinline__ long long nbr(const mlbi_params &p, const Loc &L, const float4 &e0, const float4 &e1,
+                                         int sign)
+{
+    if (L.interior) return L.r + sign * (long long)__float_as_int(e1.x);
+    int dx, dy, dz;
+    mlbi_unpack(__float_as_int(e0.w), dx, dy, dz);
+    return neighbour(p, L.x, L.y, L.z, sign * dx, sign * dy, sign * dz);
+}
+
+__host__ __device__ constexpr int pair_of(int a, int b, int S)
+{
+    return a <= b ? a * S - a * (a - 1) / 2 + (b - a) : b * S - b * (b - 1) / 2 + (a - b);
+}
+
 // ------------------------------------------------------------------ contact values
 // g_ab(xi) - g_ab(xi_ref) of the BMCSL contact value
 //   g = 1/o + 3 h xi2 / o^2 + 2 h^2 xi2^2 / o^3,   o = 1 - xi3,
@@ -127,34 +154,94 @@ __device__ __forceinline__ float bmcsl_dev(float h, float xi2r, float xi3r, floa
     return dA + dB + dC;
 }
 
-__global__ void __launch_bounds__(kBlock) k_gfield(mlbi_params p, const float4 *__restrict__ mom,
-                                                   const mlbi_entry *__restrict__ tab, float *__restrict__ dg,
-                                                   unsigned int *__restrict__ flags)
+__global__ void __launch_bounds__(kBX * kBY) k_gfield(mlbi_params p, const float4 *__restrict__ mom,
+                                                      const mlbi_entry *__restrict__ tab, float *__restrict__ dg,
+                                                      unsigned int *__restrict__ flags)
 {
+    Loc L;
+    if (!locate(p, L)) return;
+    const long long N = p.N, r = L.r;
+    float d2 = 0.f, d3 = 0.f;
+    for (int c = 0; c < p.S; ++c) {
+        float sum = 0.f;
+        int outside = 0;
+        for (int k = 0; k < p.ball_count[c]; ++k) {
+            const int e = p.ball_start[c] + k;
+            const long long q = nbr(p, L, __ldg(&tab[2 * e]), __ldg(&tab[2 * e + 1]), 1);
+            if (q < 0) ++outside;
+            else sum += mom[c * N + q].x;
+        }
+        // smoothed density minus n_ref; sites beyond a wall hold no particles
+        const float dnbar = (sum - (float)outside * p.nref[c]) * p.ball_inv[c];
+        d2 += p.xi2_coef[c] * dnbar;
+        d3 += p.xi3_coef[c] * dnbar;
+    }
+    if (!(p.xi3_ref + d3 < 1.f)) atomicOr(flags, MLBI_FLAG_XI3);
+    for (int q = 0; q < p.npairs; ++q) dg[q * N + r] = bmcsl_dev(p.pair[q].h, p.xi2_ref, p.xi3_ref, d2, d3);
+}
+
+// ------------------------------------------------------------------ centre moments
+template <int S>
+struct Centre {
+    float n[S], dn[S], j[S][3], u[S][3];
+};
+
+template <int S>
+__device__ __forceinline__ void load_centre(const mlbi_params &p, const float4 *__restrict__ mom, long long r,
+                                            Centre<S> &c)
+{
+    float rho = 0.f, m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 v = mom[a * p.N + r];
+        c.dn[a] = v.x;
+        c.n[a] = p.nref[a] + v.x;
+        c.j[a][0] = v.y; c.j[a][1] = v.z; c.j[a][2] = v.w;
+        rho += c.n[a];
+        m[0] += v.y; m[1] += v.z; m[2] += v.w;
+    }
+    const float irho = rho > 0.f ? 1.f / rho : 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const bool ok = c.n[a] > kTinyDensity;
+        const float in = ok ? 1.f / c.n[a] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.u[a][k] = ok ? c.j[a][k] * in : m[k] * irho;
+    }
+}
+
+// ------------------------------------------------------------------ moments with local contact values
+// When every smoothing ball is the single site (kappa sigma < 1), g_ab at r
+// depends on the moments at r only: one pass over f gives both.
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const float *__restrict__ f,
+                                                      float4 *__restrict__ mom, float *__restrict__ dg,
+                                                      unsigned int *__restrict__ flags)
+{
+    constexpr int NP = S * (S + 1) / 2;
     const long long N = p.N;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        site_coords(p, r, x, y, z);
         float d2 = 0.f, d3 = 0.f;
-        for (int c = 0; c < p.S; ++c) {
-            float sum = 0.f;
-            int outside = 0;
-            for (int k = 0; k < p.ball_count[c]; ++k) {
-                int dx, dy, dz;
-                mlbi_unpack(__float_as_int(__ldg(&tab[p.ball_start[c] + k].w)), dx, dy, dz);
-                long long q = neighbour(p, x, y, z, dx, dy, dz);
-                if (q < 0) ++outside;
-                else sum += mom[c * N + q].x;
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const float *fa = f + (long long)a * MLBI_Q * N + r;
+            float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+            for (int i = 0; i < MLBI_Q; ++i) {
+                const float v = __ldg(fa + i * N);
+                m0 += v;
+                if (CX[i]) mx += CX[i] * v;
+                if (CY[i]) my += CY[i] * v;
+                if (CZ[i]) mz += CZ[i] * v;
             }
-            // smoothed density minus n_ref; sites beyond a wall hold no particles
-            float dnbar = (sum - (float)outside * p.nref[c]) * p.ball_inv[c];
-            d2 += p.xi2_coef[c] * dnbar;
-            d3 += p.xi3_coef[c] * dnbar;
+            mom[a * N + r] = make_float4(m0, mx, my, mz);
+            d2 += p.xi2_coef[a] * m0;
+            d3 += p.xi3_coef[a] * m0;
         }
         if (!(p.xi3_ref + d3 < 1.f)) atomicOr(flags, MLBI_FLAG_XI3);
-        for (int q = 0; q < p.npairs; ++q)
-            dg[q * N + r] = bmcsl_dev(p.pair[q].h, p.xi2_ref, p.xi3_ref, d2, d3);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) dg[q * N + r] = bmcsl_dev(p.pair[q].h, p.xi2_ref, p.xi3_ref, d2, d3);
     }
 }
 
@@ -176,219 +263,670 @@ __device__ __forceinline__ void solve_sym3(const float G[6], const float b[3], f
     x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
 }
 
-__global__ void __launch_bounds__(kBlock) k_pass1(mlbi_params p, const float4 *__restrict__ mom,
-                                                  const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
-                                                  const float4 *__restrict__ fext, float4 *__restrict__ frest,
-                                                  float4 *__restrict__ du)
+// neighbour data of species b at r + sign*d (zero density beyond a wall)
+struct Nb {
+    float Dn, n, j0, j1, j2;
+    long long q;
+};
+
+template <bool INTERIOR>
+__device__ __forceinline__ Nb fetch_nb(const mlbi_params &p, const Loc &L, const float4 &e0, const float4 &e1,
+                                       int sign, const float4 *__restrict__ fld, float nref, float dn0, float n0)
+{
+    Nb o;
+    o.q = INTERIOR ? L.r + sign * (long long)__float_as_int(e1.x) : nbr(p, L, e0, e1, sign);
+    if (INTERIOR || o.q >= 0) {
+        const float4 v = fld[o.q];
+        o.Dn = v.x - dn0; o.n = nref + v.x; o.j0 = v.y; o.j1 = v.z; o.j2 = v.w;
+    } else {
+        o.Dn = -n0; o.n = 0.f; o.j0 = 0.f; o.j1 = 0.f; o.j2 = 0.f;
+    }
+    return o;
+}
+
+// Shell sums of pass 1 for every species a over neighbour species b:
+//   hard core  -hc_ab sum_{+-d} s (g(r)+g(r+d))/2 n^b(r+d)                   (Eq. potmeanforce)
+//   exchange   vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 (j^b(r+d) - n^b(r+d) u^a)] (Eqs. gammaab, viscousforce)
+//   friction   Gamma^a = vx_ab sum_{+-d} s s^T (g(r)+g(r+d))/2 n^b(r+d)
+template <int S, bool INTERIOR>
+__device__ __forceinline__ void pass1_shells(const mlbi_params &p, const Loc &L, const Centre<S> &c,
+                                             const float *dgc, const float4 *__restrict__ mom,
+                                             const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
+                                             float (&hc)[S][3], float (&fv)[S][3], float (&G)[S][6])
 {
     const long long N = p.N;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
-         r += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        site_coords(p, r, x, y, z);
-        SiteState c;
-        load_site(p, mom, r, c);
-        for (int a = 0; a < p.S; ++a) {
-            float hc[3] = {0.f, 0.f, 0.f}, at[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f};
-            float G[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int b = 0; b < p.S; ++b) {
-                const int pi = p.pair_index[a][b];
-                const mlbi_pair pr = p.pair[pi];
-                const float *dgp = dg + pi * N;
-                const float dg0 = dgp[r];
-                const float g0 = pr.g_ref + dg0;
-                const float n0 = c.n[b], dn0 = c.dn[b];
-                float shc[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f};
-                float sG[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int k = 0; k < pr.shell_count; ++k) {
-                    const float4 e = __ldg(&tab[pr.shell_start + k]);
-                    int dx, dy, dz;
-                    mlbi_unpack(__float_as_int(e.w), dx, dy, dz);
-                    const long long ip = neighbour(p, x, y, z, dx, dy, dz);
-                    const long long im = neighbour(p, x, y, z, -dx, -dy, -dz);
-                    float Dnp = -n0, Dgp = 0.f, np = 0.f, jp0 = 0.f, jp1 = 0.f, jp2 = 0.f;
-                    float Dnm = -n0, Dgm = 0.f, nm = 0.f, jm0 = 0.f, jm1 = 0.f, jm2 = 0.f;
-                    if (ip >= 0) {
-                        float4 v = mom[b * N + ip];
-                        Dnp = v.x - dn0; np = p.nref[b] + v.x; jp0 = v.y; jp1 = v.z; jp2 = v.w;
-                        Dgp = dgp[ip] - dg0;
-                    }
-                    if (im >= 0) {
-                        float4 v = mom[b * N + im];
-                        Dnm = v.x - dn0; nm = p.nref[b] + v.x; jm0 = v.y; jm1 = v.z; jm2 = v.w;
-                        Dgm = dgp[im] - dg0;
-                    }
-                    // (g(r)+g(r+d))/2 n(r+d) - (g(r)+g(r-d))/2 n(r-d), expanded about site r
-                    const float t = g0 * (Dnp - Dnm) + 0.5f * n0 * (Dgp - Dgm) + 0.5f * (Dgp * Dnp - Dgm * Dnm);
-                    shc[0] += e.x * t; shc[1] += e.y * t; shc[2] += e.z * t;
-                    const float gp = g0 + 0.5f * Dgp, gm = g0 + 0.5f * Dgm;
-                    float vp0, vp1, vp2, vm0, vm1, vm2;
-                    if (p.drag_only) {
-                        const float w0 = c.u[b][0] - c.u[a][0], w1 = c.u[b][1] - c.u[a][1], w2 = c.u[b][2] - c.u[a][2];
-                        vp0 = np * w0; vp1 = np * w1; vp2 = np * w2;
-                        vm0 = nm * w0; vm1 = nm * w1; vm2 = nm * w2;
-                    } else {
-                        vp0 = jp0 - np * c.u[a][0]; vp1 = jp1 - np * c.u[a][1]; vp2 = jp2 - np * c.u[a][2];
-                        vm0 = jm0 - nm * c.u[a][0]; vm1 = jm1 - nm * c.u[a][1]; vm2 = jm2 - nm * c.u[a][2];
-                    }
-                    const float w0 = gp * vp0 + gm * vm0, w1 = gp * vp1 + gm * vm1, w2 = gp * vp2 + gm * vm2;
-                    const float sd = e.x * w0 + e.y * w1 + e.z * w2;
-                    sv[0] += e.x * sd; sv[1] += e.y * sd; sv[2] += e.z * sd;
-                    const float wn = gp * np + gm * nm;
-                    sG[0] += wn * e.x * e.x; sG[1] += wn * e.y * e.y; sG[2] += wn * e.z * e.z;
-                    sG[3] += wn * e.x * e.y; sG[4] += wn * e.x * e.z; sG[5] += wn * e.y * e.z;
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const float n0 = c.n[b], dn0 = c.dn[b];
+        const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
+        const float4 *fb = mom + b * N;
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+            const float4 e0 = __ldg(&tab[2 * k]);
+            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const int mask = __float_as_int(e1.y);
+            const Nb P = fetch_nb<INTERIOR>(p, L, e0, e1, 1, fb, p.nref[b], dn0, n0);
+            const Nb M = fetch_nb<INTERIOR>(p, L, e0, e1, -1, fb, p.nref[b], dn0, n0);
+            const float sx = e0.x, sy = e0.y, sz = e0.z;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                if (!(mask & (1 << a))) continue;
+                const int q = pair_of(a, b, S);
+                const mlbi_pair &pr = p.pair[q];
+                const float *dgq = dg + q * N;
+                const float Dgp = (INTERIOR || P.q >= 0) ? dgq[P.q] - dgc[q] : 0.f;
+                const float Dgm = (INTERIOR || M.q >= 0) ? dgq[M.q] - dgc[q] : 0.f;
+                const float g0 = pr.g_ref + dgc[q];
+                // (g(r)+g(r+d))/2 n(r+d) - (g(r)+g(r-d))/2 n(r-d), expanded about site r
+                const float t = -pr.hc_pre * (g0 * (P.Dn - M.Dn) + 0.5f * n0 * (Dgp - Dgm) +
+                                              0.5f * (Dgp * P.Dn - Dgm * M.Dn));
+                hc[a][0] += sx * t; hc[a][1] += sy * t; hc[a][2] += sz * t;
+                const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
+                const float wn = gp * P.n + gm * M.n;
+                float w0, w1, w2;
+                if (p.drag_only) {
+                    w0 = wn * (c.u[b][0] - c.u[a][0]);
+                    w1 = wn * (c.u[b][1] - c.u[a][1]);
+                    w2 = wn * (c.u[b][2] - c.u[a][2]);
+                } else {
+                    w0 = gp * P.j0 + gm * M.j0 - wn * c.u[a][0];
+                    w1 = gp * P.j1 + gm * M.j1 - wn * c.u[a][1];
+                    w2 = gp * P.j2 + gm * M.j2 - wn * c.u[a][2];
                 }
-                for (int q = 0; q < 3; ++q) {
-                    hc[q] -= pr.hc_pre * shc[q];
-                    fv[q] += pr.vx_pre * sv[q];
-                }
-                for (int q = 0; q < 6; ++q) G[q] += pr.vx_pre * sG[q];
-                if (pr.attr_count > 0) {
-                    float sa[3] = {0.f, 0.f, 0.f};
-                    for (int k = 0; k < pr.attr_count; ++k) {
-                        const float4 e = __ldg(&tab[pr.attr_start + k]);
-                        int dx, dy, dz;
-                        mlbi_unpack(__float_as_int(e.w), dx, dy, dz);
-                        const long long ip = neighbour(p, x, y, z, dx, dy, dz);
-                        const long long im = neighbour(p, x, y, z, -dx, -dy, -dz);
-                        // n(r+d) - n(r-d): deviations cancel n_ref exactly inside the fluid
-                        const float np = ip >= 0 ? mom[b * N + ip].x : -p.nref[b];
-                        const float nm = im >= 0 ? mom[b * N + im].x : -p.nref[b];
-                        const float dn = np - nm;
-                        sa[0] += e.x * dn; sa[1] += e.y * dn; sa[2] += e.z * dn;
-                    }
-                    for (int q = 0; q < 3; ++q) at[q] += sa[q];
-                }
+                const float sd = sx * w0 + sy * w1 + sz * w2;
+                fv[a][0] += sx * sd; fv[a][1] += sy * sd; fv[a][2] += sz * sd;
+                G[a][0] += wn * sx * sx; G[a][1] += wn * sy * sy; G[a][2] += wn * sz * sz;
+                G[a][3] += wn * sx * sy; G[a][4] += wn * sx * sz; G[a][5] += wn * sy * sz;
             }
-            float fr[3];
-            float4 fe = p.has_fext ? fext[a * N + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-            fr[0] = hc[0] + at[0] + fe.x;
-            fr[1] = hc[1] + at[1] + fe.y;
-            fr[2] = hc[2] + at[2] + fe.z;
-            frest[a * N + r] = make_float4(fr[0], fr[1], fr[2], 0.f);
-            float s[3] = {0.f, 0.f, 0.f};
-            if (p.semi_implicit) {
-                // one Jacobi sweep of u* = u + a(u*)/2 with partner velocities held at u
-                const float rhs[3] = {0.5f * (fr[0] + fv[0]), 0.5f * (fr[1] + fv[1]), 0.5f * (fr[2] + fv[2])};
-                solve_sym3(G, rhs, s);
-            }
-            du[a * N + r] = make_float4(s[0], s[1], s[2], 0.f);
         }
     }
 }
 
-// ------------------------------------------------------------------ pass 2 + collide + stream
-__global__ void __launch_bounds__(kBlock) k_pass2_collide(mlbi_params p, const float *__restrict__ fin,
-                                                          float *__restrict__ fout, const float4 *__restrict__ mom,
-                                                          const float *__restrict__ dg,
-                                                          const mlbi_entry *__restrict__ tab,
-                                                          const float4 *__restrict__ frest,
-                                                          const float4 *__restrict__ du, double *__restrict__ acc_out)
+// attraction sum_{+d} K_ab(d) (n^b(r+d) - n^b(r-d))  (G term of Eq. potmeanforce, RPA)
+template <int S, bool INTERIOR>
+__device__ __forceinline__ void pass1_attraction(const mlbi_params &p, const Loc &L,
+                                                 const float4 *__restrict__ mom,
+                                                 const mlbi_entry *__restrict__ tab, float (&at)[S][3])
 {
     const long long N = p.N;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
-         r += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        site_coords(p, r, x, y, z);
-        SiteState c;
-        load_site(p, mom, r, c);
-        float acc[MLBI_MAXS][3];
-        float duc[MLBI_MAXS][3];
-        for (int a = 0; a < p.S; ++a) {
-            float4 v = du[a * N + r];
-            duc[a][0] = v.x; duc[a][1] = v.y; duc[a][2] = v.z;
-        }
-        for (int a = 0; a < p.S; ++a) {
-            float4 fr = frest[a * N + r];
-            float fv[3] = {0.f, 0.f, 0.f};
-            for (int b = 0; b < p.S; ++b) {
-                const int pi = p.pair_index[a][b];
-                const mlbi_pair pr = p.pair[pi];
-                const float *dgp = dg + pi * N;
-                const float dg0 = dgp[r];
-                const float g0 = pr.g_ref + dg0;
-                float sv[3] = {0.f, 0.f, 0.f};
-                for (int k = 0; k < pr.shell_count; ++k) {
-                    const float4 e = __ldg(&tab[pr.shell_start + k]);
-                    int dx, dy, dz;
-                    mlbi_unpack(__float_as_int(e.w), dx, dy, dz);
-                    const long long ip = neighbour(p, x, y, z, dx, dy, dz);
-                    const long long im = neighbour(p, x, y, z, -dx, -dy, -dz);
-                    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-                    if (ip >= 0) {
-                        const float4 v = mom[b * N + ip];
-                        const float np = p.nref[b] + v.x;
-                        const float gp = g0 + 0.5f * (dgp[ip] - dg0);
-                        float v0, v1, v2;
-                        if (p.drag_only) {
-                            v0 = np * (c.u[b][0] + duc[b][0] - c.u[a][0] - duc[a][0]);
-                            v1 = np * (c.u[b][1] + duc[b][1] - c.u[a][1] - duc[a][1]);
-                            v2 = np * (c.u[b][2] + duc[b][2] - c.u[a][2] - duc[a][2]);
-                        } else {
-                            const float4 d = du[b * N + ip];
-                            v0 = (v.y - np * c.u[a][0]) + np * (d.x - duc[a][0]);
-                            v1 = (v.z - np * c.u[a][1]) + np * (d.y - duc[a][1]);
-                            v2 = (v.w - np * c.u[a][2]) + np * (d.z - duc[a][2]);
-                        }
-                        w0 += gp * v0; w1 += gp * v1; w2 += gp * v2;
-                    }
-                    if (im >= 0) {
-                        const float4 v = mom[b * N + im];
-                        const float nm = p.nref[b] + v.x;
-                        const float gm = g0 + 0.5f * (dgp[im] - dg0);
-                        float v0, v1, v2;
-                        if (p.drag_only) {
-                            v0 = nm * (c.u[b][0] + duc[b][0] - c.u[a][0] - duc[a][0]);
-                            v1 = nm * (c.u[b][1] + duc[b][1] - c.u[a][1] - duc[a][1]);
-                            v2 = nm * (c.u[b][2] + duc[b][2] - c.u[a][2] - duc[a][2]);
-                        } else {
-                            const float4 d = du[b * N + im];
-                            v0 = (v.y - nm * c.u[a][0]) + nm * (d.x - duc[a][0]);
-                            v1 = (v.z - nm * c.u[a][1]) + nm * (d.y - duc[a][1]);
-                            v2 = (v.w - nm * c.u[a][2]) + nm * (d.z - duc[a][2]);
-                        }
-                        w0 += gm * v0; w1 += gm * v1; w2 += gm * v2;
-                    }
-                    const float sd = e.x * w0 + e.y * w1 + e.z * w2;
-                    sv[0] += e.x * sd; sv[1] += e.y * sd; sv[2] += e.z * sd;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+#pragma unroll
+        for (int b = 0; b < S; ++b) {
+            const mlbi_pair &pr = p.pair[pair_of(a, b, S)];
+            const float *nb = reinterpret_cast<const float *>(mom + b * N);
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+            for (int k = pr.attr_start; k < pr.attr_start + pr.attr_count; ++k) {
+                const float4 e0 = __ldg(&tab[2 * k]);
+                const float4 e1 = __ldg(&tab[2 * k + 1]);
+                float vp, vm;
+                if (INTERIOR) {
+                    const long long o = __float_as_int(e1.x);
+                    vp = nb[4 * (L.r + o)];
+                    vm = nb[4 * (L.r - o)];
+                } else {
+                    const long long ip = nbr(p, L, e0, e1, 1), im = nbr(p, L, e0, e1, -1);
+                    // beyond a wall n = 0, i.e. n - n_ref = -n_ref
+                    vp = ip >= 0 ? nb[4 * ip] : -p.nref[b];
+                    vm = im >= 0 ? nb[4 * im] : -p.nref[b];
                 }
-                for (int q = 0; q < 3; ++q) fv[q] += pr.vx_pre * sv[q];
+                const float d = vp - vm;        // deviations cancel n_ref exactly inside the fluid
+                s0 += e0.x * d; s1 += e0.y * d; s2 += e0.z * d;
             }
-            acc[a][0] = fr.x + fv[0];     // masses are 1
-            acc[a][1] = fr.y + fv[1];
-            acc[a][2] = fr.z + fv[2];
+            at[a][0] += s0; at[a][1] += s1; at[a][2] += s2;
         }
+    }
+}
+
+// pass 1: the shell and attraction sums at u, then du from
+// (I + Gamma/2) du = (rest + exchange)/2 (one Jacobi sweep of u* = u + a(u*)/2
+// with partner velocities held at u) and the inputs of pass 2.
+template <int S>
+__global__ void __launch_bounds__(kBX * kBY) k_pass1(const mlbi_params p, const float4 *__restrict__ mom,
+                                                     const float *__restrict__ dg,
+                                                     const mlbi_entry *__restrict__ tab,
+                                                     const float4 *__restrict__ fext, float4 *__restrict__ frest,
+                                                     float4 *__restrict__ pst, float4 *__restrict__ du_out)
+{
+    constexpr int NP = S * (S + 1) / 2;
+    Loc L;
+    if (!locate(p, L)) return;
+    const long long N = p.N, r = L.r;
+    Centre<S> c;
+    load_centre<S>(p, mom, r, c);
+    float dgc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) dgc[q] = dg[q * N + r];
+    float hc[S][3], fv[S][3], G[S][6], at[S][3];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { hc[a][k] = 0.f; fv[a][k] = 0.f; at[a][k] = 0.f; }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) G[a][k] = 0.f;
+    }
+    if (L.interior) pass1_shells<S, true>(p, L, c, dgc, mom, dg, tab, hc, fv, G);
+    else pass1_shells<S, false>(p, L, c, dgc, mom, dg, tab, hc, fv, G);
+    if (p.has_attraction) {
+        if (L.interior) pass1_attraction<S, true>(p, L, mom, tab, at);
+        else pass1_attraction<S, false>(p, L, mom, tab, at);
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 fe = p.has_fext ? fext[a * N + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float fr[3] = {hc[a][0] + at[a][0] + fe.x, hc[a][1] + at[a][1] + fe.y, hc[a][2] + at[a][2] + fe.z};
+        float d[3] = {0.f, 0.f, 0.f};
+        if (p.semi_implicit) {
+            const float rhs[3] = {0.5f * (fr[0] + fv[a][0]), 0.5f * (fr[1] + fv[a][1]), 0.5f * (fr[2] + fv[a][2])};
+            solve_sym3(G[a], rhs, d);
+        }
+        // pass 2 evaluates the exchange with the centre velocity u^a; -Gamma du completes it to u*
+        const float gd0 = G[a][0] * d[0] + G[a][3] * d[1] + G[a][4] * d[2];
+        const float gd1 = G[a][3] * d[0] + G[a][1] * d[1] + G[a][5] * d[2];
+        const float gd2 = G[a][4] * d[0] + G[a][5] * d[1] + G[a][2] * d[2];
+        if (p.drag_only) {
+            frest[a * N + r] = make_float4(fr[0], fr[1], fr[2], 0.f);
+            du_out[a * N + r] = make_float4(d[0], d[1], d[2], 0.f);
+        } else {
+            frest[a * N + r] = make_float4(fr[0] - gd0, fr[1] - gd1, fr[2] - gd2, 0.f);
+        }
+        pst[a * N + r] = make_float4(c.dn[a], c.j[a][0] + c.n[a] * d[0], c.j[a][1] + c.n[a] * d[1],
+                                     c.j[a][2] + c.n[a] * d[2]);
+    }
+}
+
+// ------------------------------------------------------------------ pass 2: acceleration
+// a^a = frest^a + vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 (p*^b(r+d) - n^b(r+d) u^a)]
+// with p* = j + n du from pass 1 (drag only: partner velocity u*^b(r)).
+template <int S, bool INTERIOR>
+__device__ __forceinline__ void pass2_shells(const mlbi_params &p, const Loc &L, const Centre<S> &c,
+                                             const float *dgc, const float (&us)[S][3],
+                                             const float4 *__restrict__ pst, const float *__restrict__ dg,
+                                             const mlbi_entry *__restrict__ tab, float (&acc)[S][3])
+{
+    const long long N = p.N;
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
+        const float4 *fb = pst + b * N;
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+            const float4 e0 = __ldg(&tab[2 * k]);
+            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const int mask = __float_as_int(e1.y);
+            const Nb P = fetch_nb<INTERIOR>(p, L, e0, e1, 1, fb, p.nref[b], 0.f, 0.f);
+            const Nb M = fetch_nb<INTERIOR>(p, L, e0, e1, -1, fb, p.nref[b], 0.f, 0.f);
+            const float sx = e0.x, sy = e0.y, sz = e0.z;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                if (!(mask & (1 << a))) continue;
+                const int q = pair_of(a, b, S);
+                const mlbi_pair &pr = p.pair[q];
+                const float *dgq = dg + q * N;
+                const float Dgp = (INTERIOR || P.q >= 0) ? dgq[P.q] - dgc[q] : 0.f;
+                const float Dgm = (INTERIOR || M.q >= 0) ? dgq[M.q] - dgc[q] : 0.f;
+                const float g0 = pr.g_ref + dgc[q];
+                const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
+                const float wn = gp * P.n + gm * M.n;
+                float w0, w1, w2;
+                if (p.drag_only) {
+                    w0 = wn * (us[b][0] - us[a][0]);
+                    w1 = wn * (us[b][1] - us[a][1]);
+                    w2 = wn * (us[b][2] - us[a][2]);
+                } else {
+                    w0 = gp * P.j0 + gm * M.j0 - wn * c.u[a][0];
+                    w1 = gp * P.j1 + gm * M.j1 - wn * c.u[a][1];
+                    w2 = gp * P.j2 + gm * M.j2 - wn * c.u[a][2];
+                }
+                const float sd = sx * w0 + sy * w1 + sz * w2;
+                acc[a][0] += sx * sd; acc[a][1] += sy * sd; acc[a][2] += sz * sd;   // masses are 1
+            }
+        }
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const float4 *__restrict__ mom,
+                                                     const float *__restrict__ dg,
+                                                     const mlbi_entry *__restrict__ tab,
+                                                     const float4 *__restrict__ frest,
+                                                     const float4 *__restrict__ pst,
+                                                     const float4 *__restrict__ du, float4 *__restrict__ acc_f,
+                                                     double *__restrict__ acc_out)
+{
+    constexpr int NP = S * (S + 1) / 2;
+    Loc L;
+    if (!locate(p, L)) return;
+    const long long N = p.N, r = L.r;
+    Centre<S> c;
+    load_centre<S>(p, mom, r, c);
+    float dgc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) dgc[q] = dg[q * N + r];
+    float us[S][3];                 // partner velocities at r (drag only)
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        if (p.drag_only) {
+            const float4 v = du[a * N + r];
+            us[a][0] = c.u[a][0] + v.x; us[a][1] = c.u[a][1] + v.y; us[a][2] = c.u[a][2] + v.z;
+        } else {
+            us[a][0] = 0.f; us[a][1] = 0.f; us[a][2] = 0.f;
+        }
+    }
+    float acc[S][3];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 fr = frest[a * N + r];
+        acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
+    }
+    if (L.interior) pass2_shells<S, true>(p, L, c, dgc, us, pst, dg, tab, acc);
+    else pass2_shells<S, false>(p, L, c, dgc, us, pst, dg, tab, acc);
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
         if (acc_out) {
-            for (int a = 0; a < p.S; ++a)
-                for (int q = 0; q < 3; ++q) acc_out[(a * 3 + q) * N + r] = (double)acc[a][q];
-            continue;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc_out[(a * 3 + q) * N + r] = (double)acc[a][q];
+        } else {
+            acc_f[a * N + r] = make_float4(acc[a][0], acc[a][1], acc[a][2], 0.f);
         }
+    }
+}
 
-        // velocities of the equilibrium: u^a + a^a/2 (semi-implicit) or u^a, and their barycentre
-        const float half = p.semi_implicit ? 0.5f : 0.f;
-        float ueq[MLBI_MAXS][3];
-        float ub[3] = {0.f, 0.f, 0.f}, rho = 0.f;
-        for (int a = 0; a < p.S; ++a) {
-            for (int q = 0; q < 3; ++q) {
-                ueq[a][q] = c.u[a][q] + half * acc[a][q];
-                ub[q] += c.n[a] * ueq[a][q];
+// ------------------------------------------------------------------ shared-memory tiles (z marching)
+// A block of 32 x 4 threads owns a 32 x 4 column of sites and marches up z
+// through `zchunk` planes.  The stencil field of every species (float4: the
+// moments in pass 1, (n - n_ref, p*) in pass 2) and the contact-value
+// deviations of every pair are staged in shared memory as a ring of planes
+// of (32 + 2R) x (4 + 2R) sites: 2R + 1 planes in use and one more being
+// filled by cp.async while the current plane is computed.  Every shell
+// neighbour is then read from shared memory.
+template <int S, int R>
+struct Tile {
+    static constexpr int TX = kBX, TY = kBY;
+    static constexpr int TXH = TX + 2 * R, TYH = TY + 2 * R, PLANE = TXH * TYH;
+    static constexpr int NSLOT = 2 * R + 2;
+    static constexpr int NP = S * (S + 1) / 2;
+    static constexpr size_t bytes = (size_t)NSLOT * PLANE * (S * sizeof(float4) + NP * sizeof(float));
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int wrap_or_out(int c, int L, bool wall)
+{
+    if (wall) return (c < 0 || c >= L) ? -1 : c;
+    c %= L;
+    return c < 0 ? c + L : c;
+}
+
+// Stage plane gz of the tile with corner (x0 - R, y0 - R) into ring slot `slot`.
+// Sites beyond a wall get n = 0 (n - n_ref = -n_ref), zero momentum and g = g_ref.
+template <int S, int R>
+__device__ __forceinline__ void stage_plane(const mlbi_params &p, int x0, int y0, int gz, int slot,
+                                            const float4 *__restrict__ fld, const float *__restrict__ dg,
+                                            float4 *sf, float *sg)
+{
+    using T = Tile<S, R>;
+    const long long N = p.N;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const int z = wrap_or_out(gz, p.nz, p.wall_axis == 2);
+    for (int idx = tid; idx < T::PLANE; idx += kBX * kBY) {
+        const int hx = idx % T::TXH, hy = idx / T::TXH;
+        const int x = wrap_or_out(x0 - R + hx, p.nx, p.wall_axis == 0);
+        const int y = wrap_or_out(y0 - R + hy, p.ny, p.wall_axis == 1);
+        float4 *df = sf + (size_t)slot * S * T::PLANE + idx;
+        float *dgs = sg + (size_t)slot * T::NP * T::PLANE + idx;
+        if (x < 0 || y < 0 || z < 0) {
+#pragma unroll
+            for (int b = 0; b < S; ++b) df[b * T::PLANE] = make_float4(-p.nref[b], 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < T::NP; ++q) dgs[q * T::PLANE] = 0.f;
+        } else {
+            const long long g = x + (long long)p.nx * (y + (long long)p.ny * z);
+#pragma unroll
+            for (int b = 0; b < S; ++b) cp_async16(df + b * T::PLANE, fld + b * N + g);
+#pragma unroll
+            for (int q = 0; q < T::NP; ++q) cp_async4(dgs + q * T::PLANE, dg + q * N + g);
+        }
+    }
+}
+
+// ring slot of plane z0 - R + k
+__device__ __forceinline__ int ring(int k, int nslot) { return k % nslot; }
+
+// Shell sums of pass 1 from the tile (same sums as pass1_shells).
+template <int S, int R>
+__device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
+                                                  const float4 *sf, const float *sg, int kz,
+                                                  int cidx, const Centre<S> &c, const float *dgc,
+                                                  float (&hc)[S][3], float (&fv)[S][3], float (&G)[S][6])
+{
+    using T = Tile<S, R>;
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const float n0 = c.n[b], dn0 = c.dn[b], nr = p.nref[b];
+        const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+            const float4 e0 = __ldg(&tab[2 * k]);
+            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
+            const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);   // ring slots of the +-d planes
+            const float4 vp = sf[(size_t)sp * S * T::PLANE + b * T::PLANE + cidx + off];
+            const float4 vm = sf[(size_t)sm * S * T::PLANE + b * T::PLANE + cidx - off];
+            const float Dnp = vp.x - dn0, np = nr + vp.x, Dnm = vm.x - dn0, nm = nr + vm.x;
+            const float sx = e0.x, sy = e0.y, sz = e0.z;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                if (!(mask & (1 << a))) continue;
+                const int q = pair_of(a, b, S);
+                const mlbi_pair &pr = p.pair[q];
+                const float Dgp = sg[(size_t)sp * T::NP * T::PLANE + q * T::PLANE + cidx + off] - dgc[q];
+                const float Dgm = sg[(size_t)sm * T::NP * T::PLANE + q * T::PLANE + cidx - off] - dgc[q];
+                const float g0 = pr.g_ref + dgc[q];
+                const float t = -pr.hc_pre * (g0 * (Dnp - Dnm) + 0.5f * n0 * (Dgp - Dgm) +
+                                              0.5f * (Dgp * Dnp - Dgm * Dnm));
+                hc[a][0] += sx * t; hc[a][1] += sy * t; hc[a][2] += sz * t;
+                const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
+                const float wn = gp * np + gm * nm;
+                float w0, w1, w2;
+                if (p.drag_only) {
+                    w0 = wn * (c.u[b][0] - c.u[a][0]);
+                    w1 = wn * (c.u[b][1] - c.u[a][1]);
+                    w2 = wn * (c.u[b][2] - c.u[a][2]);
+                } else {
+                    w0 = gp * vp.y + gm * vm.y - wn * c.u[a][0];
+                    w1 = gp * vp.z + gm * vm.z - wn * c.u[a][1];
+                    w2 = gp * vp.w + gm * vm.w - wn * c.u[a][2];
+                }
+                const float sd = sx * w0 + sy * w1 + sz * w2;
+                fv[a][0] += sx * sd; fv[a][1] += sy * sd; fv[a][2] += sz * sd;
+                G[a][0] += wn * sx * sx; G[a][1] += wn * sy * sy; G[a][2] += wn * sz * sz;
+                G[a][3] += wn * sx * sy; G[a][4] += wn * sx * sz; G[a][5] += wn * sy * sz;
             }
-            rho += c.n[a];
         }
-        const float irho = rho > 0.f ? 1.f / rho : 0.f;
-        ub[0] *= irho; ub[1] *= irho; ub[2] *= irho;
-        const float ubub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-        const float omega = p.omega;
+    }
+}
 
-        for (int a = 0; a < p.S; ++a) {
-            const float na = c.n[a], dna = c.dn[a];
-            const float *fa = fin + (long long)a * MLBI_Q * N + r;
-            float *oa = fout + (long long)a * MLBI_Q * N;
-            const float ua0 = ueq[a][0], ua1 = ueq[a][1], ua2 = ueq[a][2];
-            const float a0 = acc[a][0], a1 = acc[a][1], a2 = acc[a][2];
-            const float trM = 2.f * (ua0 * ub[0] + ua1 * ub[1] + ua2 * ub[2]) - ubub;   // tr(ua u + u ua - u u)
-            const float trS = 2.f * (ub[0] * a0 + ub[1] * a1 + ub[2] * a2);             // tr(u a + a u)
-            const float ks = p.src_scale * na;
+template <int S>
+__device__ __forceinline__ void centre_from(const mlbi_params &p, const float4 (&v)[S], Centre<S> &c)
+{
+    float rho = 0.f, m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        c.dn[a] = v[a].x;
+        c.n[a] = p.nref[a] + v[a].x;
+        c.j[a][0] = v[a].y; c.j[a][1] = v[a].z; c.j[a][2] = v[a].w;
+        rho += c.n[a];
+        m[0] += v[a].y; m[1] += v[a].z; m[2] += v[a].w;
+    }
+    const float irho = rho > 0.f ? 1.f / rho : 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const bool ok = c.n[a] > kTinyDensity;
+        const float in = ok ? 1.f / c.n[a] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.u[a][k] = ok ? c.j[a][k] * in : m[k] * irho;
+    }
+}
+
+// finish pass 1 at one site: predictor and outputs (shared by both pass-1 kernels)
+template <int S>
+__device__ __forceinline__ void pass1_finish(const mlbi_params &p, long long r, const Centre<S> &c,
+                                             const float (&hc)[S][3], const float (&fv)[S][3],
+                                             const float (&G)[S][6], const float (&at)[S][3],
+                                             const float4 *__restrict__ fext, float4 *__restrict__ frest,
+                                             float4 *__restrict__ pst, float4 *__restrict__ du_out)
+{
+    const long long N = p.N;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 fe = p.has_fext ? fext[a * N + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float fr[3] = {hc[a][0] + at[a][0] + fe.x, hc[a][1] + at[a][1] + fe.y, hc[a][2] + at[a][2] + fe.z};
+        float d[3] = {0.f, 0.f, 0.f};
+        if (p.semi_implicit) {
+            // one Jacobi sweep of u* = u + a(u*)/2 with partner velocities held at u
+            const float rhs[3] = {0.5f * (fr[0] + fv[a][0]), 0.5f * (fr[1] + fv[a][1]), 0.5f * (fr[2] + fv[a][2])};
+            solve_sym3(G[a], rhs, d);
+        }
+        // pass 2 evaluates the exchange with the centre velocity u^a; -Gamma du completes it to u*
+        const float gd0 = G[a][0] * d[0] + G[a][3] * d[1] + G[a][4] * d[2];
+        const float gd1 = G[a][3] * d[0] + G[a][1] * d[1] + G[a][5] * d[2];
+        const float gd2 = G[a][4] * d[0] + G[a][5] * d[1] + G[a][2] * d[2];
+        if (p.drag_only) {
+            frest[a * N + r] = make_float4(fr[0], fr[1], fr[2], 0.f);
+            du_out[a * N + r] = make_float4(d[0], d[1], d[2], 0.f);
+        } else {
+            frest[a * N + r] = make_float4(fr[0] - gd0, fr[1] - gd1, fr[2] - gd2, 0.f);
+        }
+        pst[a * N + r] = make_float4(c.dn[a], c.j[a][0] + c.n[a] * d[0], c.j[a][1] + c.n[a] * d[1],
+                                     c.j[a][2] + c.n[a] * d[2]);
+    }
+}
+
+template <int S, int R>
+__global__ void __launch_bounds__(kBX * kBY, 4) k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom,
+                                                              const float *__restrict__ dg,
+                                                              const mlbi_entry *__restrict__ tab,
+                                                              const float4 *__restrict__ fext,
+                                                              float4 *__restrict__ frest, float4 *__restrict__ pst,
+                                                              float4 *__restrict__ du_out)
+{
+    using T = Tile<S, R>;
+    extern __shared__ float4 smem[];
+    float4 *sf = smem;                                                      // [NSLOT][S][PLANE]
+    float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);   // [NSLOT][NP][PLANE]
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int z1 = min(z0 + p.zchunk, p.nz);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool active = x < p.nx && y < p.ny;
+    const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, x0, y0, z0 - R + k, ring(k, T::NSLOT), mom, dg, sf, sg);
+    cp_async_commit();
+    for (int z = z0; z < z1; ++z) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int kz = z - z0 + R;                      // ring position of plane z
+        if (z + 1 < z1) {
+            stage_plane<S, R>(p, x0, y0, z + R + 1, ring(kz + R + 1, T::NSLOT), mom, dg, sf, sg);
+            cp_async_commit();
+        }
+        if (!active) continue;
+        const int cs = ring(kz, T::NSLOT);
+        float4 cv[S];
+#pragma unroll
+        for (int a = 0; a < S; ++a) cv[a] = sf[(size_t)cs * S * T::PLANE + a * T::PLANE + cidx];
+        Centre<S> c;
+        centre_from<S>(p, cv, c);
+        float dgc[T::NP];
+#pragma unroll
+        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[(size_t)cs * T::NP * T::PLANE + q * T::PLANE + cidx];
+        float hc[S][3], fv[S][3], G[S][6], at[S][3];
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { hc[a][k] = 0.f; fv[a][k] = 0.f; at[a][k] = 0.f; }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) G[a][k] = 0.f;
+        }
+        pass1_tile_shells<S, R>(p, tab, sf, sg, kz, cidx, c, dgc, hc, fv, G);
+        const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
+        if (p.has_attraction) {
+            Loc L;
+            L.x = x; L.y = y; L.z = z; L.r = r;
+            const int Rr = p.reach;
+            L.interior = x >= Rr && x < p.nx - Rr && y >= Rr && y < p.ny - Rr && z >= Rr && z < p.nz - Rr;
+            if (L.interior) pass1_attraction<S, true>(p, L, mom, tab, at);
+            else pass1_attraction<S, false>(p, L, mom, tab, at);
+        }
+        pass1_finish<S>(p, r, c, hc, fv, G, at, fext, frest, pst, du_out);
+    }
+}
+
+template <int S, int R>
+__global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params p, const float4 *__restrict__ mom,
+                                                              const float *__restrict__ dg,
+                                                              const mlbi_entry *__restrict__ tab,
+                                                              const float4 *__restrict__ frest,
+                                                              const float4 *__restrict__ pst,
+                                                              const float4 *__restrict__ du,
+                                                              float4 *__restrict__ acc_f, double *__restrict__ acc_out)
+{
+    using T = Tile<S, R>;
+    extern __shared__ float4 smem[];
+    float4 *sf = smem;
+    float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);
+    const long long N = p.N;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int z1 = min(z0 + p.zchunk, p.nz);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool active = x < p.nx && y < p.ny;
+    const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, x0, y0, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    cp_async_commit();
+    for (int z = z0; z < z1; ++z) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int kz = z - z0 + R;
+        if (z + 1 < z1) {
+            stage_plane<S, R>(p, x0, y0, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
+            cp_async_commit();
+        }
+        if (!active) continue;
+        const int cs = ring(kz, T::NSLOT);
+        const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
+        Centre<S> c;
+        load_centre<S>(p, mom, r, c);
+        float dgc[T::NP];
+#pragma unroll
+        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[(size_t)cs * T::NP * T::PLANE + q * T::PLANE + cidx];
+        float us[S][3];
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            if (p.drag_only) {
+                const float4 v = du[a * N + r];
+                us[a][0] = c.u[a][0] + v.x; us[a][1] = c.u[a][1] + v.y; us[a][2] = c.u[a][2] + v.z;
+            } else {
+                us[a][0] = 0.f; us[a][1] = 0.f; us[a][2] = 0.f;
+            }
+        }
+        float acc[S][3];
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const float4 fr = frest[a * N + r];
+            acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
+        }
+#pragma unroll
+        for (int b = 0; b < S; ++b) {
+            const float nr = p.nref[b];
+            const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
+#pragma unroll 2
+            for (int k = k0; k < k1; ++k) {
+                const float4 e0 = __ldg(&tab[2 * k]);
+                const float4 e1 = __ldg(&tab[2 * k + 1]);
+                const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
+                const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);
+                const float4 vp = sf[(size_t)sp * S * T::PLANE + b * T::PLANE + cidx + off];
+                const float4 vm = sf[(size_t)sm * S * T::PLANE + b * T::PLANE + cidx - off];
+                const float np = nr + vp.x, nm = nr + vm.x;
+                const float sx = e0.x, sy = e0.y, sz = e0.z;
+#pragma unroll
+                for (int a = 0; a < S; ++a) {
+                    if (!(mask & (1 << a))) continue;
+                    const int q = pair_of(a, b, S);
+                    const mlbi_pair &pr = p.pair[q];
+                    const float Dgp = sg[(size_t)sp * T::NP * T::PLANE + q * T::PLANE + cidx + off] - dgc[q];
+                    const float Dgm = sg[(size_t)sm * T::NP * T::PLANE + q * T::PLANE + cidx - off] - dgc[q];
+                    const float g0 = pr.g_ref + dgc[q];
+                    const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
+                    const float wn = gp * np + gm * nm;
+                    float w0, w1, w2;
+                    if (p.drag_only) {
+                        w0 = wn * (us[b][0] - us[a][0]);
+                        w1 = wn * (us[b][1] - us[a][1]);
+                        w2 = wn * (us[b][2] - us[a][2]);
+                    } else {
+                        w0 = gp * vp.y + gm * vm.y - wn * c.u[a][0];
+                        w1 = gp * vp.z + gm * vm.z - wn * c.u[a][1];
+                        w2 = gp * vp.w + gm * vm.w - wn * c.u[a][2];
+                    }
+                    const float sd = sx * w0 + sy * w1 + sz * w2;
+                    acc[a][0] += sx * sd; acc[a][1] += sy * sd; acc[a][2] += sz * sd;   // masses are 1
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            if (acc_out) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc_out[(a * 3 + q) * N + r] = (double)acc[a][q];
+            } else {
+                acc_f[a * N + r] = make_float4(acc[a][0], acc[a][1], acc[a][2], 0.f);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ collide + stream
+// Collision toward psi_perp at u + a/2 (Eq. prefactor, Hermite-2) with the
+// forcing of Eq. evolution scaled by (1 - omega/2), push streaming with
+// halfway bounce-back.  Pure streaming: 19 loads and 19 stores per species-site.
+template <int S>
+__global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, const float *__restrict__ fin,
+                                                       float *__restrict__ fout, const float4 *__restrict__ mom,
+                                                       const float4 *__restrict__ accf)
+{
+    Loc L;
+    if (!locate(p, L)) return;
+    const long long N = p.N, r = L.r;
+    Centre<S> c;
+    load_centre<S>(p, mom, r, c);
+    const float half = p.semi_implicit ? 0.5f : 0.f;
+    float ueq[S][3], acc[S][3];
+    float ub[3] = {0.f, 0.f, 0.f}, rho = 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 v = accf[a * N + r];
+        acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            ueq[a][q] = c.u[a][q] + half * acc[a][q];
+            ub[q] += c.n[a] * ueq[a][q];
+        }
+        rho += c.n[a];
+    }
+    const float irho = rho > 0.f ? 1.f / rho : 0.f;
+    ub[0] *= irho; ub[1] *= irho; ub[2] *= irho;
+    const float ubub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+    const float omega = p.omega;
+    const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+    const bool inner = L.x >= 1 && L.x < p.nx - 1 && L.y >= 1 && L.y < p.ny - 1 && L.z >= 1 && L.z < p.nz - 1;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float na = c.n[a], dna = c.dn[a];
+        const float *fa = fin + (long long)a * MLBI_Q * N + r;
+        float *oa = fout + (long long)a * MLBI_Q * N;
+        const float ua0 = ueq[a][0], ua1 = ueq[a][1], ua2 = ueq[a][2];
+        const float a0 = acc[a][0], a1 = acc[a][1], a2 = acc[a][2];
+        const float trM = 2.f * (ua0 * ub[0] + ua1 * ub[1] + ua2 * ub[2]) - ubub;   // tr(ua u + u ua - u u)
+        const float trS = 2.f * (ub[0] * a0 + ub[1] * a1 + ub[2] * a2);             // tr(u a + a u)
+        const float ks = p.src_scale * na;
+        if (inner) {
+            // interior: every link lands at r + c_i; fully unrolled, no branches
+            float fi[MLBI_Q];
+#pragma unroll
+            for (int i = 0; i < MLBI_Q; ++i) fi[i] = __ldg(fa + i * N);
 #pragma unroll
             for (int i = 0; i < MLBI_Q; ++i) {
                 const float cu = CX[i] * ua0 + CY[i] * ua1 + CZ[i] * ua2;
@@ -397,18 +935,31 @@ __global__ void __launch_bounds__(kBlock) k_pass2_collide(mlbi_params p, const f
                 // psi_perp - w n_ref  (1/cs2 = 3, 1/(2 cs4) = 4.5, 1/(2 cs2) = 1.5)
                 const float psi = WQ[i] * (dna + na * (3.f * cu + 4.5f * (2.f * cu * cb - cb * cb) - 1.5f * trM));
                 const float src = WQ[i] * ks * (3.f * ca + 9.f * cb * ca - 1.5f * trS);
-                const float fi = __ldg(fa + i * N);
-                const float post = fi - omega * (fi - psi) + src;
-                const long long q = neighbour(p, x, y, z, CX[i], CY[i], CZ[i]);
+                oa[i * N + r + CX[i] + CY[i] * sy + CZ[i] * sz] = fi[i] - omega * (fi[i] - psi) + src;
+            }
+        } else {
+            // faces: periodic wrap or halfway bounce-back; compact loop
+#pragma unroll 1
+            for (int i = 0; i < MLBI_Q; ++i) {
+                const int cx = CXv(i), cy = CYv(i), cz = CZv(i);
+                const float w = WQv(i);
+                const float cu = cx * ua0 + cy * ua1 + cz * ua2;
+                const float cb = cx * ub[0] + cy * ub[1] + cz * ub[2];
+                const float ca = cx * a0 + cy * a1 + cz * a2;
+                const float psi = w * (dna + na * (3.f * cu + 4.5f * (2.f * cu * cb - cb * cb) - 1.5f * trM));
+                const float src = w * ks * (3.f * ca + 9.f * cb * ca - 1.5f * trS);
+                const float fv = __ldg(fa + i * N);
+                const float post = fv - omega * (fv - psi) + src;
+                const long long q = neighbour(p, L.x, L.y, L.z, cx, cy, cz);
                 if (q >= 0) {
                     oa[i * N + q] = post;
                 } else {
                     const int ax = p.wall_axis;
-                    const int cax = ax == 0 ? CX[i] : (ax == 1 ? CY[i] : CZ[i]);
-                    const int xa = ax == 0 ? x : (ax == 1 ? y : z);
+                    const int cax = ax == 0 ? cx : (ax == 1 ? cy : cz);
+                    const int xa = ax == 0 ? L.x : (ax == 1 ? L.y : L.z);
                     const float *uw = (xa + cax < 0) ? p.wall_lo : p.wall_hi;
-                    const float cuw = CX[i] * uw[0] + CY[i] * uw[1] + CZ[i] * uw[2];
-                    oa[opposite(i) * N + r] = post - 6.f * WQ[i] * na * cuw;
+                    const float cuw = cx * uw[0] + cy * uw[1] + cz * uw[2];
+                    oa[opposite(i) * N + r] = post - 6.f * w * na * cuw;
                 }
             }
         }
@@ -538,14 +1089,6 @@ __global__ void k_conservation_final(mlbi_params p, const double *__restrict__ p
     }
 }
 
-inline unsigned grid_for(long long N)
-{
-    long long g = (N + kBlock - 1) / kBlock;
-    if (g < 1) g = 1;
-    if (g > (1ll << 30)) g = 1ll << 30;
-    return (unsigned)g;
-}
-
 }  // namespace
 
 cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
@@ -554,23 +1097,80 @@ cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int
     return cudaGetLastError();
 }
 
+dim3 tiled_grid(const mlbi_params &p)
+{
+    return dim3((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY), (unsigned)p.nz);
+}
+
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
 {
-    k_gfield<<<grid_for(p.N), kBlock, 0, s>>>(p, b.mom, b.table, b.dg, b.flags);
+    k_gfield<<<tiled_grid(p), dim3(kBX, kBY), 0, s>>>(p, b.mom, b.table, b.dg, b.flags);
+    return cudaGetLastError();
+}
+
+#define MLBI_DISPATCH_S(...)                                                                       \
+    switch (p.S) {                                                                                 \
+    case 1: { constexpr int SS = 1; __VA_ARGS__; } break;                                          \
+    case 2: { constexpr int SS = 2; __VA_ARGS__; } break;                                          \
+    case 3: { constexpr int SS = 3; __VA_ARGS__; } break;                                          \
+    case 4: { constexpr int SS = 4; __VA_ARGS__; } break;                                          \
+    default: return cudaErrorInvalidValue;                                                         \
+    }
+
+cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+{
+    MLBI_DISPATCH_S((k_moments_g<SS><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags)));
+    return cudaGetLastError();
+}
+
+template <int S, int R>
+cudaError_t launch_pass1_tiled(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
+{
+    using T = Tile<S, R>;
+    auto k = k_pass1_tiled<S, R>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+    if (e != cudaSuccess) return e;
+    const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
+                 (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+    k<<<g, dim3(kBX, kBY), T::bytes, s>>>(p, b.mom, b.dg, b.table, b.fext, b.frest, b.pst, b.du);
+    return cudaGetLastError();
+}
+
+template <int S, int R>
+cudaError_t launch_pass2_tiled(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
+{
+    using T = Tile<S, R>;
+    auto k = k_pass2_tiled<S, R>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+    if (e != cudaSuccess) return e;
+    const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
+                 (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+    k<<<g, dim3(kBX, kBY), T::bytes, s>>>(p, b.mom, b.dg, b.table, b.frest, b.pst, b.du, b.acc, acc_out);
     return cudaGetLastError();
 }
 
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
 {
-    k_pass1<<<grid_for(p.N), kBlock, 0, s>>>(p, b.mom, b.dg, b.table, b.fext, b.frest, b.du);
+    if (p.tile_r == 1) { MLBI_DISPATCH_S(return launch_pass1_tiled<SS, 1>(p, b, s)); }
+    if (p.tile_r == 2) { MLBI_DISPATCH_S(return launch_pass1_tiled<SS, 2>(p, b, s)); }
+    const dim3 g = tiled_grid(p), t(kBX, kBY);
+    MLBI_DISPATCH_S((k_pass1<SS><<<g, t, 0, s>>>(p, b.mom, b.dg, b.table, b.fext, b.frest, b.pst, b.du)));
     return cudaGetLastError();
 }
 
-cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, double *acc_out,
-                                      cudaStream_t s)
+cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
 {
-    k_pass2_collide<<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.f[cur ^ 1], b.mom, b.dg, b.table, b.frest,
-                                                     b.du, acc_out);
+    if (p.tile_r == 1) { MLBI_DISPATCH_S(return launch_pass2_tiled<SS, 1>(p, b, acc_out, s)); }
+    if (p.tile_r == 2) { MLBI_DISPATCH_S(return launch_pass2_tiled<SS, 2>(p, b, acc_out, s)); }
+    const dim3 g = tiled_grid(p), t(kBX, kBY);
+    MLBI_DISPATCH_S((k_pass2<SS><<<g, t, 0, s>>>(p, b.mom, b.dg, b.table, b.frest, b.pst, b.du, b.acc, acc_out)));
+    return cudaGetLastError();
+}
+
+cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+{
+    const dim3 g = tiled_grid(p), t(kBX, kBY);
+    MLBI_DISPATCH_S((k_collide<SS><<<g, t, 0, s>>>(p, b.f[cur], b.f[cur ^ 1], b.mom, b.acc)));
     return cudaGetLastError();
 }
 

@@ -245,3 +245,22 @@ def test_full_size_sampled(gpu, orc):
             expect[a, i] = post[:, i, a, perm[i]] - wg[i] * nref[a]
             got[a, i] = f_t1[a, i, sites]
     assert rel(got, expect) < TOL_STATE
+
+
+@pytest.mark.parametrize("sigma,shape,wall_axis", [
+    ([1.0, 1.5], (37, 9, 19), 1),      # shell reach 1: 2 x-tiles (one partial), 3 y-tiles, 2 z-chunks
+    ([1.0, 2.0], (45, 11, 35), 2),     # shell reach 2, walls normal to z
+    ([1.25, 1.5, 2.0], (33, 7, 18), -1),
+])
+def test_tiled_kernels_ragged_boxes(gpu, orc, sigma, shape, wall_axis):
+    """The shared-memory tiled force passes on boxes that leave partial tiles
+    and partial z-chunks, periodic and with walls on different axes."""
+    S = len(sigma)
+    lat = W.Lattice(shape=shape, sigma=sigma, tau=0.9, wall_axis=wall_axis,
+                    wall_u_lo=tuple(0.0 if k == wall_axis else (0.01 if k == 0 else 0.0) for k in range(3)) if wall_axis >= 0 else (0, 0, 0),
+                    wall_u_hi=tuple(0.0 if k == wall_axis else (-0.02 if k == 0 else 0.0) for k in range(3)) if wall_axis >= 0 else (0, 0, 0))
+    n0 = W.densities_from_packing(0.15, sigma, [1.0 / S] * S)
+    n = W.noise(lat, n0, 0.05, seed=31)
+    u = W.random_velocities(lat, 0.005, seed=32)
+    w = run_pair(gpu, orc, lat, n, u, checkpoints=(0, 1, 25))
+    assert w["n"] < TOL_STATE and w["u"] < TOL_STATE and w["acc"] < TOL_ACC, w
