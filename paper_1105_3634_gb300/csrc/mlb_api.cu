@@ -231,6 +231,23 @@ mlb_status rebuild(mlb_ctx *c)
         if (p.ball_count[g] != 1) p.local_g = 0;
     p.tile_r = tile_r;
     p.zchunk = std::min(c->desc.nz, 16);
+    // the 13 canonical half offsets of the 3x3x3 cube, in the order the kernels use:
+    // (1,0,0); (-1,1,0), (0,1,0), (1,1,0); then dz = 1 with dy = -1, 0, 1 and dx = -1, 0, 1
+    {
+        int cube[13][3], k = 0;
+        cube[k][0] = 1; cube[k][1] = 0; cube[k][2] = 0; ++k;
+        for (int dx = -1; dx <= 1; ++dx) { cube[k][0] = dx; cube[k][1] = 1; cube[k][2] = 0; ++k; }
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) { cube[k][0] = dx; cube[k][1] = dy; cube[k][2] = 1; ++k; }
+        for (int a2 = 0; a2 < S; ++a2)
+            for (int b2 = a2; b2 < S; ++b2) {
+                const double sab = 0.5 * (c->sigma[a2] + c->sigma[b2]);
+                int m = 0;
+                for (int j = 0; j < 13; ++j)
+                    if (in_shell(sab, cube[j][0], cube[j][1], cube[j][2])) m |= 1 << j;
+                p.cube_mask[p.pair_index[a2][b2]] = m;
+            }
+    }
     p.reach = maxoff;
     p.xi2_ref = (float)xi2;
     p.xi3_ref = (float)xi3;
@@ -303,7 +320,14 @@ mlb_status forces(mlb_ctx *c)
         { Timed t(c, K_GFIELD); MLB_CUDA(c, mlbi_launch_gfield(c->p, c->b, c->stream)); }
     }
     { Timed t(c, K_PASS1); MLB_CUDA(c, mlbi_launch_pass1(c->p, c->b, c->stream)); }
+    return MLB_OK;
+}
+
+// pass 2, collision and streaming of one step (after forces())
+mlb_status advance(mlb_ctx *c)
+{
     { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
+    { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream)); }
     return MLB_OK;
 }
 
@@ -585,10 +609,8 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
     for (int64_t t = 0; t < nsteps; ++t) {
         st = forces(c);
         if (st != MLB_OK) return st;
-        {
-            Timed tm(c, K_COLLIDE);
-            MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream));
-        }
+        st = advance(c);
+        if (st != MLB_OK) return st;
         c->cur ^= 1;
         ++c->step;
     }
@@ -597,7 +619,8 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
-    return (c && c->p.local_g) ? K_NKINDS - 1 : K_NKINDS;
+    if (!c) return 0;
+    return (c->p.local_g ? 1 : 2) + 3;
 }
 
 const char *mlb_kernel_name(int32_t k)

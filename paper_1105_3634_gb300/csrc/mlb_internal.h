@@ -60,6 +60,7 @@ struct mlbi_params {
     int reach;                       // largest offset component of any stencil (>= 1)
     int local_g;                     // every smoothing ball is the single site
     int tile_r;                      // reach of the union shells if the tiled kernels serve it (1, 2), else 0
+    int cube_mask[MLBI_MAXP];        // tile_r == 1: bit k set when half offset k of the 3x3x3 cube is in S_ab
     int zchunk;                      // planes per block of the tiled kernels
     int pair_index[MLBI_MAXS][MLBI_MAXS];
     mlbi_pair pair[MLBI_MAXP];

@@ -3,10 +3,10 @@
 //
 // Storage (structure of arrays, x fastest, site r = x + nx (y + ny z)):
 //   f[a][i][r]  FP32 populations minus w_i n_ref^a      (76 B per species-site)
-//   mom[a][r]   float4 (n - n_ref, j_x, j_y, j_z)        (16 B per species-site)
+//   mom[a][r]   float4 (n - n_ref, u_x, u_y, u_z)        (16 B per species-site)
 //   dg[p][r]    g_ab - g_ab(reference densities)          (per unordered pair)
 //   frest[a][r] F^hc + G + F_ext - Gamma du               (pass 1 -> pass 2)
-//   pst[a][r]   (n - n_ref, j + n du)                     (pass 1 -> pass 2)
+//   pst[a][r]   (n - n_ref, u + du)                       (pass 1 -> pass 2)
 //
 // One step (all launches on one stream):
 //   k_moments        f -> mom                                    (Eq. colonna)
@@ -19,8 +19,9 @@
 //   k_collide        collision toward psi_perp at u + a/2 with      (Eqs. evolution, prefactor)
 //                    (1 - omega/2) forcing, push streaming /
 //                    halfway bounce-back
-// Deviations from reference values (n - n_ref, g - g_ref) keep the FP32
-// differences that the contact sums take small and exact where they cancel.
+// Deviations from reference values (n - n_ref, g - g_ref) and velocities
+// (rather than momenta) keep the FP32 differences that the contact sums take
+// between neighbouring sites small and exact.
 #include "mlb_internal.h"
 
 #include <math.h>
@@ -74,25 +75,58 @@ __device__ __forceinline__ long long neighbour(const mlbi_params &p, int x, int 
 }
 
 // ------------------------------------------------------------------ moments
-__global__ void __launch_bounds__(kBlock) k_moments(mlbi_params p, const float *__restrict__ f,
+// dn = sum_i f_i (f stored minus w_i n_ref), j = sum_i c_i f_i taken as the
+// differences of opposite links first, u = j / n (the barycentric velocity
+// where n is tiny).  Writes (dn, u) of every species.
+template <int S>
+__device__ __forceinline__ void site_moments(const mlbi_params &p, const float *__restrict__ f, long long r,
+                                             float (&dn)[S], float (&u)[S][3])
+{
+    const long long N = p.N;
+    float jx[S], jy[S], jz[S], rho = 0.f, m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float *fa = f + (long long)a * MLBI_Q * N + r;
+        float v[MLBI_Q];
+#pragma unroll
+        for (int i = 0; i < MLBI_Q; ++i) v[i] = __ldg(fa + i * N);
+        float m0 = v[0], mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int i = 1; i < MLBI_Q; i += 2) {
+            m0 += v[i] + v[i + 1];
+            const float d = v[i] - v[i + 1];          // opposite links i, i + 1
+            if (CX[i]) mx += CX[i] * d;
+            if (CY[i]) my += CY[i] * d;
+            if (CZ[i]) mz += CZ[i] * d;
+        }
+        dn[a] = m0;
+        jx[a] = mx; jy[a] = my; jz[a] = mz;
+        rho += p.nref[a] + m0;
+        m[0] += mx; m[1] += my; m[2] += mz;
+    }
+    const float irho = rho > 0.f ? 1.f / rho : 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float n = p.nref[a] + dn[a];
+        const bool ok = n > kTinyDensity;
+        const float in = ok ? 1.f / n : 0.f;
+        u[a][0] = ok ? jx[a] * in : m[0] * irho;
+        u[a][1] = ok ? jy[a] * in : m[1] * irho;
+        u[a][2] = ok ? jz[a] * in : m[2] * irho;
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_moments(const mlbi_params p, const float *__restrict__ f,
                                                     float4 *__restrict__ mom)
 {
     const long long N = p.N;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
-        for (int a = 0; a < p.S; ++a) {
-            const float *fa = f + (long long)a * MLBI_Q * N + r;
-            float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+        float dn[S], u[S][3];
+        site_moments<S>(p, f, r, dn, u);
 #pragma unroll
-            for (int i = 0; i < MLBI_Q; ++i) {
-                float v = __ldg(fa + i * N);
-                m0 += v;
-                if (CX[i]) mx += CX[i] * v;
-                if (CY[i]) my += CY[i] * v;
-                if (CZ[i]) mz += CZ[i] * v;
-            }
-            mom[a * N + r] = make_float4(m0, mx, my, mz);
-        }
+        for (int a = 0; a < S; ++a) mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
     }
 }
 
@@ -183,30 +217,19 @@ __global__ void __launch_bounds__(kBX * kBY) k_gfield(mlbi_params p, const float
 // ------------------------------------------------------------------ centre moments
 template <int S>
 struct Centre {
-    float n[S], dn[S], j[S][3], u[S][3];
+    float n[S], dn[S], u[S][3];
 };
 
 template <int S>
 __device__ __forceinline__ void load_centre(const mlbi_params &p, const float4 *__restrict__ mom, long long r,
                                             Centre<S> &c)
 {
-    float rho = 0.f, m[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < S; ++a) {
         const float4 v = mom[a * p.N + r];
         c.dn[a] = v.x;
         c.n[a] = p.nref[a] + v.x;
-        c.j[a][0] = v.y; c.j[a][1] = v.z; c.j[a][2] = v.w;
-        rho += c.n[a];
-        m[0] += v.y; m[1] += v.z; m[2] += v.w;
-    }
-    const float irho = rho > 0.f ? 1.f / rho : 0.f;
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const bool ok = c.n[a] > kTinyDensity;
-        const float in = ok ? 1.f / c.n[a] : 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) c.u[a][k] = ok ? c.j[a][k] * in : m[k] * irho;
+        c.u[a][0] = v.y; c.u[a][1] = v.z; c.u[a][2] = v.w;
     }
 }
 
@@ -222,22 +245,14 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
     const long long N = p.N;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
+        float dn[S], u[S][3];
+        site_moments<S>(p, f, r, dn, u);
         float d2 = 0.f, d3 = 0.f;
 #pragma unroll
         for (int a = 0; a < S; ++a) {
-            const float *fa = f + (long long)a * MLBI_Q * N + r;
-            float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-            for (int i = 0; i < MLBI_Q; ++i) {
-                const float v = __ldg(fa + i * N);
-                m0 += v;
-                if (CX[i]) mx += CX[i] * v;
-                if (CY[i]) my += CY[i] * v;
-                if (CZ[i]) mz += CZ[i] * v;
-            }
-            mom[a * N + r] = make_float4(m0, mx, my, mz);
-            d2 += p.xi2_coef[a] * m0;
-            d3 += p.xi3_coef[a] * m0;
+            mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
+            d2 += p.xi2_coef[a] * dn[a];
+            d3 += p.xi3_coef[a] * dn[a];
         }
         if (!(p.xi3_ref + d3 < 1.f)) atomicOr(flags, MLBI_FLAG_XI3);
 #pragma unroll
@@ -265,7 +280,7 @@ __device__ __forceinline__ void solve_sym3(const float G[6], const float b[3], f
 
 // neighbour data of species b at r + sign*d (zero density beyond a wall)
 struct Nb {
-    float Dn, n, j0, j1, j2;
+    float Dn, n, u0, u1, u2;
     long long q;
 };
 
@@ -277,16 +292,16 @@ __device__ __forceinline__ Nb fetch_nb(const mlbi_params &p, const Loc &L, const
     o.q = INTERIOR ? L.r + sign * (long long)__float_as_int(e1.x) : nbr(p, L, e0, e1, sign);
     if (INTERIOR || o.q >= 0) {
         const float4 v = fld[o.q];
-        o.Dn = v.x - dn0; o.n = nref + v.x; o.j0 = v.y; o.j1 = v.z; o.j2 = v.w;
+        o.Dn = v.x - dn0; o.n = nref + v.x; o.u0 = v.y; o.u1 = v.z; o.u2 = v.w;
     } else {
-        o.Dn = -n0; o.n = 0.f; o.j0 = 0.f; o.j1 = 0.f; o.j2 = 0.f;
+        o.Dn = -n0; o.n = 0.f; o.u0 = 0.f; o.u1 = 0.f; o.u2 = 0.f;
     }
     return o;
 }
 
 // Shell sums of pass 1 for every species a over neighbour species b:
 //   hard core  -hc_ab sum_{+-d} s (g(r)+g(r+d))/2 n^b(r+d)                   (Eq. potmeanforce)
-//   exchange   vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 (j^b(r+d) - n^b(r+d) u^a)] (Eqs. gammaab, viscousforce)
+//   exchange   vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 n^b(r+d) (u^b(r+d) - u^a)]  (Eqs. gammaab, viscousforce)
 //   friction   Gamma^a = vx_ab sum_{+-d} s s^T (g(r)+g(r+d))/2 n^b(r+d)
 template <int S, bool INTERIOR>
 __device__ __forceinline__ void pass1_shells(const mlbi_params &p, const Loc &L, const Centre<S> &c,
@@ -329,9 +344,10 @@ __device__ __forceinline__ void pass1_shells(const mlbi_params &p, const Loc &L,
                     w1 = wn * (c.u[b][1] - c.u[a][1]);
                     w2 = wn * (c.u[b][2] - c.u[a][2]);
                 } else {
-                    w0 = gp * P.j0 + gm * M.j0 - wn * c.u[a][0];
-                    w1 = gp * P.j1 + gm * M.j1 - wn * c.u[a][1];
-                    w2 = gp * P.j2 + gm * M.j2 - wn * c.u[a][2];
+                    const float hp = gp * P.n, hm = gm * M.n;
+                    w0 = hp * (P.u0 - c.u[a][0]) + hm * (M.u0 - c.u[a][0]);
+                    w1 = hp * (P.u1 - c.u[a][1]) + hm * (M.u1 - c.u[a][1]);
+                    w2 = hp * (P.u2 - c.u[a][2]) + hm * (M.u2 - c.u[a][2]);
                 }
                 const float sd = sx * w0 + sy * w1 + sz * w2;
                 fv[a][0] += sx * sd; fv[a][1] += sy * sd; fv[a][2] += sz * sd;
@@ -431,14 +447,13 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass1(const mlbi_params p, const 
         } else {
             frest[a * N + r] = make_float4(fr[0] - gd0, fr[1] - gd1, fr[2] - gd2, 0.f);
         }
-        pst[a * N + r] = make_float4(c.dn[a], c.j[a][0] + c.n[a] * d[0], c.j[a][1] + c.n[a] * d[1],
-                                     c.j[a][2] + c.n[a] * d[2]);
+        pst[a * N + r] = make_float4(c.dn[a], c.u[a][0] + d[0], c.u[a][1] + d[1], c.u[a][2] + d[2]);
     }
 }
 
 // ------------------------------------------------------------------ pass 2: acceleration
-// a^a = frest^a + vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 (p*^b(r+d) - n^b(r+d) u^a)]
-// with p* = j + n du from pass 1 (drag only: partner velocity u*^b(r)).
+// a^a = frest^a + vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 n^b(r+d) (u*^b(r+d) - u^a)]
+// with u* = u + du from pass 1 (drag only: partner velocity u*^b(r)).
 template <int S, bool INTERIOR>
 __device__ __forceinline__ void pass2_shells(const mlbi_params &p, const Loc &L, const Centre<S> &c,
                                              const float *dgc, const float (&us)[S][3],
@@ -475,9 +490,10 @@ __device__ __forceinline__ void pass2_shells(const mlbi_params &p, const Loc &L,
                     w1 = wn * (us[b][1] - us[a][1]);
                     w2 = wn * (us[b][2] - us[a][2]);
                 } else {
-                    w0 = gp * P.j0 + gm * M.j0 - wn * c.u[a][0];
-                    w1 = gp * P.j1 + gm * M.j1 - wn * c.u[a][1];
-                    w2 = gp * P.j2 + gm * M.j2 - wn * c.u[a][2];
+                    const float hp = gp * P.n, hm = gm * M.n;
+                    w0 = hp * (P.u0 - c.u[a][0]) + hm * (M.u0 - c.u[a][0]);
+                    w1 = hp * (P.u1 - c.u[a][1]) + hm * (M.u1 - c.u[a][1]);
+                    w2 = hp * (P.u2 - c.u[a][2]) + hm * (M.u2 - c.u[a][2]);
                 }
                 const float sd = sx * w0 + sy * w1 + sz * w2;
                 acc[a][0] += sx * sd; acc[a][1] += sy * sd; acc[a][2] += sz * sd;   // masses are 1
@@ -531,6 +547,18 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const 
             acc_f[a * N + r] = make_float4(acc[a][0], acc[a][1], acc[a][2], 0.f);
         }
     }
+}
+
+// The 13 canonical half offsets of the 3x3x3 cube (first non-zero of (dz, dy, dx)
+// positive); with reach 1 every contact shell is a subset of them.
+__device__ constexpr int KX[13] = {1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1};
+__device__ constexpr int KY[13] = {0, 1, 1, 1, -1, -1, -1, 0, 0, 0, 1, 1, 1};
+__device__ constexpr int KZ[13] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+
+__device__ __forceinline__ float cube_inv_len(int k)
+{
+    const int q = KX[k] * KX[k] + KY[k] * KY[k] + KZ[k] * KZ[k];
+    return q == 1 ? 1.0f : (q == 2 ? 0.70710678118654752f : 0.57735026918962576f);
 }
 
 // ------------------------------------------------------------------ shared-memory tiles (z marching)
@@ -623,8 +651,8 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
             const float4 e1 = __ldg(&tab[2 * k + 1]);
             const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
             const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);   // ring slots of the +-d planes
-            const float4 vp = sf[(size_t)sp * S * T::PLANE + b * T::PLANE + cidx + off];
-            const float4 vm = sf[(size_t)sm * S * T::PLANE + b * T::PLANE + cidx - off];
+            const float4 vp = sf[sp * S * T::PLANE + b * T::PLANE + cidx + off];
+            const float4 vm = sf[sm * S * T::PLANE + b * T::PLANE + cidx - off];
             const float Dnp = vp.x - dn0, np = nr + vp.x, Dnm = vm.x - dn0, nm = nr + vm.x;
             const float sx = e0.x, sy = e0.y, sz = e0.z;
 #pragma unroll
@@ -632,8 +660,8 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
                 if (!(mask & (1 << a))) continue;
                 const int q = pair_of(a, b, S);
                 const mlbi_pair &pr = p.pair[q];
-                const float Dgp = sg[(size_t)sp * T::NP * T::PLANE + q * T::PLANE + cidx + off] - dgc[q];
-                const float Dgm = sg[(size_t)sm * T::NP * T::PLANE + q * T::PLANE + cidx - off] - dgc[q];
+                const float Dgp = sg[sp * T::NP * T::PLANE + q * T::PLANE + cidx + off] - dgc[q];
+                const float Dgm = sg[sm * T::NP * T::PLANE + q * T::PLANE + cidx - off] - dgc[q];
                 const float g0 = pr.g_ref + dgc[q];
                 const float t = -pr.hc_pre * (g0 * (Dnp - Dnm) + 0.5f * n0 * (Dgp - Dgm) +
                                               0.5f * (Dgp * Dnp - Dgm * Dnm));
@@ -646,9 +674,10 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
                     w1 = wn * (c.u[b][1] - c.u[a][1]);
                     w2 = wn * (c.u[b][2] - c.u[a][2]);
                 } else {
-                    w0 = gp * vp.y + gm * vm.y - wn * c.u[a][0];
-                    w1 = gp * vp.z + gm * vm.z - wn * c.u[a][1];
-                    w2 = gp * vp.w + gm * vm.w - wn * c.u[a][2];
+                    const float hp = gp * np, hm = gm * nm;
+                    w0 = hp * (vp.y - c.u[a][0]) + hm * (vm.y - c.u[a][0]);
+                    w1 = hp * (vp.z - c.u[a][1]) + hm * (vm.z - c.u[a][1]);
+                    w2 = hp * (vp.w - c.u[a][2]) + hm * (vm.w - c.u[a][2]);
                 }
                 const float sd = sx * w0 + sy * w1 + sz * w2;
                 fv[a][0] += sx * sd; fv[a][1] += sy * sd; fv[a][2] += sz * sd;
@@ -659,25 +688,149 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
     }
 }
 
+// Pass-1 shell sums for reach 1: the 13 half offsets of the 3x3x3 cube are
+// compile-time constants, so the unit vectors are immediates and their zero
+// components drop out; cube_mask[pair] selects the offsets of each shell.
+template <int S>
+__device__ __forceinline__ void pass1_cube_shells(const mlbi_params &p, const float4 *sf, const float *sg, int kz,
+                                                  int cidx, const Centre<S> &c, const float *dgc,
+                                                  float (&hc)[S][3], float (&fv)[S][3], float (&G)[S][6])
+{
+    using T = Tile<S, 1>;
+    // ring slots of the planes z - 1, z, z + 1 as element offsets (32-bit)
+    const int s4[3] = {ring(kz - 1, T::NSLOT) * S * T::PLANE + cidx, ring(kz, T::NSLOT) * S * T::PLANE + cidx,
+                       ring(kz + 1, T::NSLOT) * S * T::PLANE + cidx};
+    const int s1[3] = {ring(kz - 1, T::NSLOT) * T::NP * T::PLANE + cidx, ring(kz, T::NSLOT) * T::NP * T::PLANE + cidx,
+                       ring(kz + 1, T::NSLOT) * T::NP * T::PLANE + cidx};
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const float n0 = c.n[b], dn0 = c.dn[b], nr = p.nref[b];
+        int any = 0;
+#pragma unroll
+        for (int a = 0; a < S; ++a) any |= p.cube_mask[pair_of(a, b, S)];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            if (!((any >> k) & 1)) continue;
+            const int off = KX[k] + T::TXH * KY[k];
+            const float4 vp = sf[s4[1 + KZ[k]] + b * T::PLANE + off];
+            const float4 vm = sf[s4[1 - KZ[k]] + b * T::PLANE - off];
+            const float dDn = vp.x - vm.x, np = nr + vp.x, nm = nr + vm.x;
+            const float il = cube_inv_len(k);
+            const float sx = KX[k] * il, sy = KY[k] * il, sz = KZ[k] * il;
+            const bool hx = KX[k] != 0, hy = KY[k] != 0, hz = KZ[k] != 0;
+            // s . u at +-d, shared by every species a
+            float sjp = 0.f, sjm = 0.f;
+            if (hx) { sjp += sx * vp.y; sjm += sx * vm.y; }
+            if (hy) { sjp += sy * vp.z; sjm += sy * vm.z; }
+            if (hz) { sjp += sz * vp.w; sjm += sz * vm.w; }
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                const int q = pair_of(a, b, S);
+                if (!((p.cube_mask[q] >> k) & 1)) continue;
+                const mlbi_pair &pr = p.pair[q];
+                const float Dgp = sg[s1[1 + KZ[k]] + q * T::PLANE + off] - dgc[q];
+                const float Dgm = sg[s1[1 - KZ[k]] + q * T::PLANE - off] - dgc[q];
+                const float g0 = pr.g_ref + dgc[q];
+                // (g(r)+g(r+d))/2 n(r+d) - (g(r)+g(r-d))/2 n(r-d) = g0 (n+ - n-) + (n+ Dg+ - n- Dg-)/2
+                const float t = -pr.hc_pre * (g0 * dDn + 0.5f * (np * Dgp - nm * Dgm));
+                if (hx) hc[a][0] += sx * t;
+                if (hy) hc[a][1] += sy * t;
+                if (hz) hc[a][2] += sz * t;
+                const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
+                const float wn = gp * np + gm * nm;
+                float su = 0.f;                    // s . u^a (drag only: s . (u^b - u^a))
+                if (p.drag_only) {
+                    if (hx) su += sx * (c.u[a][0] - c.u[b][0]);
+                    if (hy) su += sy * (c.u[a][1] - c.u[b][1]);
+                    if (hz) su += sz * (c.u[a][2] - c.u[b][2]);
+                } else {
+                    if (hx) su += sx * c.u[a][0];
+                    if (hy) su += sy * c.u[a][1];
+                    if (hz) su += sz * c.u[a][2];
+                }
+                const float sd = p.drag_only ? -wn * su : gp * np * (sjp - su) + gm * nm * (sjm - su);
+                if (hx) fv[a][0] += sx * sd;
+                if (hy) fv[a][1] += sy * sd;
+                if (hz) fv[a][2] += sz * sd;
+                if (hx) G[a][0] += wn * (sx * sx);
+                if (hy) G[a][1] += wn * (sy * sy);
+                if (hz) G[a][2] += wn * (sz * sz);
+                if (hx && hy) G[a][3] += wn * (sx * sy);
+                if (hx && hz) G[a][4] += wn * (sx * sz);
+                if (hy && hz) G[a][5] += wn * (sy * sz);
+            }
+        }
+    }
+}
+
+// Pass-2 exchange sums for reach 1 (the cube specialisation of the table loop).
+template <int S>
+__device__ __forceinline__ void pass2_cube_shells(const mlbi_params &p, const float4 *sf, const float *sg, int kz,
+                                                  int cidx, const Centre<S> &c, const float *dgc,
+                                                  const float (&us)[S][3], float (&acc)[S][3])
+{
+    using T = Tile<S, 1>;
+    const int s4[3] = {ring(kz - 1, T::NSLOT) * S * T::PLANE + cidx, ring(kz, T::NSLOT) * S * T::PLANE + cidx,
+                       ring(kz + 1, T::NSLOT) * S * T::PLANE + cidx};
+    const int s1[3] = {ring(kz - 1, T::NSLOT) * T::NP * T::PLANE + cidx, ring(kz, T::NSLOT) * T::NP * T::PLANE + cidx,
+                       ring(kz + 1, T::NSLOT) * T::NP * T::PLANE + cidx};
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const float nr = p.nref[b];
+        int any = 0;
+#pragma unroll
+        for (int a = 0; a < S; ++a) any |= p.cube_mask[pair_of(a, b, S)];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            if (!((any >> k) & 1)) continue;
+            const int off = KX[k] + T::TXH * KY[k];
+            const float4 vp = sf[s4[1 + KZ[k]] + b * T::PLANE + off];
+            const float4 vm = sf[s4[1 - KZ[k]] + b * T::PLANE - off];
+            const float np = nr + vp.x, nm = nr + vm.x;
+            const float il = cube_inv_len(k);
+            const float sx = KX[k] * il, sy = KY[k] * il, sz = KZ[k] * il;
+            const bool hx = KX[k] != 0, hy = KY[k] != 0, hz = KZ[k] != 0;
+            float sjp = 0.f, sjm = 0.f;              // s . u* at +-d, shared by every species a
+            if (hx) { sjp += sx * vp.y; sjm += sx * vm.y; }
+            if (hy) { sjp += sy * vp.z; sjm += sy * vm.z; }
+            if (hz) { sjp += sz * vp.w; sjm += sz * vm.w; }
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                const int q = pair_of(a, b, S);
+                if (!((p.cube_mask[q] >> k) & 1)) continue;
+                const mlbi_pair &pr = p.pair[q];
+                const float Dgp = sg[s1[1 + KZ[k]] + q * T::PLANE + off] - dgc[q];
+                const float Dgm = sg[s1[1 - KZ[k]] + q * T::PLANE - off] - dgc[q];
+                const float g0 = pr.g_ref + dgc[q];
+                const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
+                const float wn = gp * np + gm * nm;
+                float su = 0.f;                    // s . u^a (drag only: s . (u*^a - u*^b))
+                if (p.drag_only) {
+                    if (hx) su += sx * (us[a][0] - us[b][0]);
+                    if (hy) su += sy * (us[a][1] - us[b][1]);
+                    if (hz) su += sz * (us[a][2] - us[b][2]);
+                } else {
+                    if (hx) su += sx * c.u[a][0];
+                    if (hy) su += sy * c.u[a][1];
+                    if (hz) su += sz * c.u[a][2];
+                }
+                const float sd = p.drag_only ? -wn * su : gp * np * (sjp - su) + gm * nm * (sjm - su);
+                if (hx) acc[a][0] += sx * sd;     // masses are 1
+                if (hy) acc[a][1] += sy * sd;
+                if (hz) acc[a][2] += sz * sd;
+            }
+        }
+    }
+}
+
 template <int S>
 __device__ __forceinline__ void centre_from(const mlbi_params &p, const float4 (&v)[S], Centre<S> &c)
 {
-    float rho = 0.f, m[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < S; ++a) {
         c.dn[a] = v[a].x;
         c.n[a] = p.nref[a] + v[a].x;
-        c.j[a][0] = v[a].y; c.j[a][1] = v[a].z; c.j[a][2] = v[a].w;
-        rho += c.n[a];
-        m[0] += v[a].y; m[1] += v[a].z; m[2] += v[a].w;
-    }
-    const float irho = rho > 0.f ? 1.f / rho : 0.f;
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const bool ok = c.n[a] > kTinyDensity;
-        const float in = ok ? 1.f / c.n[a] : 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) c.u[a][k] = ok ? c.j[a][k] * in : m[k] * irho;
+        c.u[a][0] = v[a].y; c.u[a][1] = v[a].z; c.u[a][2] = v[a].w;
     }
 }
 
@@ -710,8 +863,7 @@ __device__ __forceinline__ void pass1_finish(const mlbi_params &p, long long r, 
         } else {
             frest[a * N + r] = make_float4(fr[0] - gd0, fr[1] - gd1, fr[2] - gd2, 0.f);
         }
-        pst[a * N + r] = make_float4(c.dn[a], c.j[a][0] + c.n[a] * d[0], c.j[a][1] + c.n[a] * d[1],
-                                     c.j[a][2] + c.n[a] * d[2]);
+        pst[a * N + r] = make_float4(c.dn[a], c.u[a][0] + d[0], c.u[a][1] + d[1], c.u[a][2] + d[2]);
     }
 }
 
@@ -746,12 +898,12 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass1_tiled(const mlbi_params 
         const int cs = ring(kz, T::NSLOT);
         float4 cv[S];
 #pragma unroll
-        for (int a = 0; a < S; ++a) cv[a] = sf[(size_t)cs * S * T::PLANE + a * T::PLANE + cidx];
+        for (int a = 0; a < S; ++a) cv[a] = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
         Centre<S> c;
         centre_from<S>(p, cv, c);
         float dgc[T::NP];
 #pragma unroll
-        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[(size_t)cs * T::NP * T::PLANE + q * T::PLANE + cidx];
+        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[cs * T::NP * T::PLANE + q * T::PLANE + cidx];
         float hc[S][3], fv[S][3], G[S][6], at[S][3];
 #pragma unroll
         for (int a = 0; a < S; ++a) {
@@ -760,7 +912,8 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass1_tiled(const mlbi_params 
 #pragma unroll
             for (int k = 0; k < 6; ++k) G[a][k] = 0.f;
         }
-        pass1_tile_shells<S, R>(p, tab, sf, sg, kz, cidx, c, dgc, hc, fv, G);
+        if constexpr (R == 1) pass1_cube_shells<S>(p, sf, sg, kz, cidx, c, dgc, hc, fv, G);
+        else pass1_tile_shells<S, R>(p, tab, sf, sg, kz, cidx, c, dgc, hc, fv, G);
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
         if (p.has_attraction) {
             Loc L;
@@ -810,7 +963,7 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params 
         load_centre<S>(p, mom, r, c);
         float dgc[T::NP];
 #pragma unroll
-        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[(size_t)cs * T::NP * T::PLANE + q * T::PLANE + cidx];
+        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[cs * T::NP * T::PLANE + q * T::PLANE + cidx];
         float us[S][3];
 #pragma unroll
         for (int a = 0; a < S; ++a) {
@@ -827,6 +980,9 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params 
             const float4 fr = frest[a * N + r];
             acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
         }
+        if constexpr (R == 1) {
+            pass2_cube_shells<S>(p, sf, sg, kz, cidx, c, dgc, us, acc);
+        } else {
 #pragma unroll
         for (int b = 0; b < S; ++b) {
             const float nr = p.nref[b];
@@ -837,8 +993,8 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params 
                 const float4 e1 = __ldg(&tab[2 * k + 1]);
                 const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
                 const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);
-                const float4 vp = sf[(size_t)sp * S * T::PLANE + b * T::PLANE + cidx + off];
-                const float4 vm = sf[(size_t)sm * S * T::PLANE + b * T::PLANE + cidx - off];
+                const float4 vp = sf[sp * S * T::PLANE + b * T::PLANE + cidx + off];
+                const float4 vm = sf[sm * S * T::PLANE + b * T::PLANE + cidx - off];
                 const float np = nr + vp.x, nm = nr + vm.x;
                 const float sx = e0.x, sy = e0.y, sz = e0.z;
 #pragma unroll
@@ -846,8 +1002,8 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params 
                     if (!(mask & (1 << a))) continue;
                     const int q = pair_of(a, b, S);
                     const mlbi_pair &pr = p.pair[q];
-                    const float Dgp = sg[(size_t)sp * T::NP * T::PLANE + q * T::PLANE + cidx + off] - dgc[q];
-                    const float Dgm = sg[(size_t)sm * T::NP * T::PLANE + q * T::PLANE + cidx - off] - dgc[q];
+                    const float Dgp = sg[sp * T::NP * T::PLANE + q * T::PLANE + cidx + off] - dgc[q];
+                    const float Dgm = sg[sm * T::NP * T::PLANE + q * T::PLANE + cidx - off] - dgc[q];
                     const float g0 = pr.g_ref + dgc[q];
                     const float gp = pr.vx_pre * (g0 + 0.5f * Dgp), gm = pr.vx_pre * (g0 + 0.5f * Dgm);
                     const float wn = gp * np + gm * nm;
@@ -857,14 +1013,16 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params 
                         w1 = wn * (us[b][1] - us[a][1]);
                         w2 = wn * (us[b][2] - us[a][2]);
                     } else {
-                        w0 = gp * vp.y + gm * vm.y - wn * c.u[a][0];
-                        w1 = gp * vp.z + gm * vm.z - wn * c.u[a][1];
-                        w2 = gp * vp.w + gm * vm.w - wn * c.u[a][2];
+                        const float hp = gp * np, hm = gm * nm;
+                        w0 = hp * (vp.y - c.u[a][0]) + hm * (vm.y - c.u[a][0]);
+                        w1 = hp * (vp.z - c.u[a][1]) + hm * (vm.z - c.u[a][1]);
+                        w2 = hp * (vp.w - c.u[a][2]) + hm * (vm.w - c.u[a][2]);
                     }
                     const float sd = sx * w0 + sy * w1 + sz * w2;
                     acc[a][0] += sx * sd; acc[a][1] += sy * sd; acc[a][2] += sz * sd;   // masses are 1
                 }
             }
+        }
         }
 #pragma unroll
         for (int a = 0; a < S; ++a) {
@@ -880,25 +1038,19 @@ __global__ void __launch_bounds__(kBX * kBY, 4) k_pass2_tiled(const mlbi_params 
 
 // ------------------------------------------------------------------ collide + stream
 // Collision toward psi_perp at u + a/2 (Eq. prefactor, Hermite-2) with the
-// forcing of Eq. evolution scaled by (1 - omega/2), push streaming with
-// halfway bounce-back.  Pure streaming: 19 loads and 19 stores per species-site.
+// forcing of Eq. evolution scaled by (1 - omega/2), then push streaming:
+// f(r + c_i) with periodic wrap by selects, or halfway bounce-back at walls.
 template <int S>
-__global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, const float *__restrict__ fin,
-                                                       float *__restrict__ fout, const float4 *__restrict__ mom,
-                                                       const float4 *__restrict__ accf)
+__device__ __forceinline__ void collide_push(const mlbi_params &p, int x, int y, int z, long long r,
+                                             const Centre<S> &c, const float (&acc)[S][3],
+                                             const float *__restrict__ fin, float *__restrict__ fout)
 {
-    Loc L;
-    if (!locate(p, L)) return;
-    const long long N = p.N, r = L.r;
-    Centre<S> c;
-    load_centre<S>(p, mom, r, c);
+    const long long N = p.N;
     const float half = p.semi_implicit ? 0.5f : 0.f;
-    float ueq[S][3], acc[S][3];
+    float ueq[S][3];
     float ub[3] = {0.f, 0.f, 0.f}, rho = 0.f;
 #pragma unroll
     for (int a = 0; a < S; ++a) {
-        const float4 v = accf[a * N + r];
-        acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             ueq[a][q] = c.u[a][q] + half * acc[a][q];
@@ -911,34 +1063,54 @@ __global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, c
     const float ubub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
     const float omega = p.omega;
     const long long sy = p.nx, sz = (long long)p.nx * p.ny;
-    const bool inner = L.x >= 1 && L.x < p.nx - 1 && L.y >= 1 && L.y < p.ny - 1 && L.z >= 1 && L.z < p.nz - 1;
+    // links that wrap around a periodic face move by -+ the extent; sites next
+    // to a wall take the compact bounce-back path
+    const bool wall_site = (p.wall_axis == 0 && (x == 0 || x == p.nx - 1)) ||
+                           (p.wall_axis == 1 && (y == 0 || y == p.ny - 1)) ||
+                           (p.wall_axis == 2 && (z == 0 || z == p.nz - 1));
+    const long long wxm = x == 0 ? p.nx : 0, wxp = x == p.nx - 1 ? -(long long)p.nx : 0;
+    const long long wym = y == 0 ? sz : 0, wyp = y == p.ny - 1 ? -sz : 0;
+    const long long wzm = z == 0 ? N : 0, wzp = z == p.nz - 1 ? -N : 0;
 #pragma unroll
     for (int a = 0; a < S; ++a) {
         const float na = c.n[a], dna = c.dn[a];
-        const float *fa = fin + (long long)a * MLBI_Q * N + r;
         float *oa = fout + (long long)a * MLBI_Q * N;
+        const float *fa = fin + (long long)a * MLBI_Q * N + r;
+        float fi[MLBI_Q];
+#pragma unroll
+        for (int i = 0; i < MLBI_Q; ++i) fi[i] = __ldg(fa + i * N);
         const float ua0 = ueq[a][0], ua1 = ueq[a][1], ua2 = ueq[a][2];
         const float a0 = acc[a][0], a1 = acc[a][1], a2 = acc[a][2];
         const float trM = 2.f * (ua0 * ub[0] + ua1 * ub[1] + ua2 * ub[2]) - ubub;   // tr(ua u + u ua - u u)
         const float trS = 2.f * (ub[0] * a0 + ub[1] * a1 + ub[2] * a2);             // tr(u a + a u)
         const float ks = p.src_scale * na;
-        if (inner) {
-            // interior: every link lands at r + c_i; fully unrolled, no branches
-            float fi[MLBI_Q];
+        if (!wall_site) {
+            // psi_perp and the forcing split into parts even and odd in c_i:
+            // direction i and its opposite share the even part and flip the odd one.
+            const float om1 = 1.f - omega;
+            const float K1 = dna - 1.5f * na * trM;          // even part of psi at c = 0
+            const float K2 = -1.5f * ks * trS;                // even part of the forcing at c = 0
+            float *o = oa + r;
+            o[0] = om1 * fi[0] + WQ[0] * (omega * K1 + K2);
 #pragma unroll
-            for (int i = 0; i < MLBI_Q; ++i) fi[i] = __ldg(fa + i * N);
-#pragma unroll
-            for (int i = 0; i < MLBI_Q; ++i) {
+            for (int i = 1; i < MLBI_Q; i += 2) {
                 const float cu = CX[i] * ua0 + CY[i] * ua1 + CZ[i] * ua2;
                 const float cb = CX[i] * ub[0] + CY[i] * ub[1] + CZ[i] * ub[2];
                 const float ca = CX[i] * a0 + CY[i] * a1 + CZ[i] * a2;
-                // psi_perp - w n_ref  (1/cs2 = 3, 1/(2 cs4) = 4.5, 1/(2 cs2) = 1.5)
-                const float psi = WQ[i] * (dna + na * (3.f * cu + 4.5f * (2.f * cu * cb - cb * cb) - 1.5f * trM));
-                const float src = WQ[i] * ks * (3.f * ca + 9.f * cb * ca - 1.5f * trS);
-                oa[i * N + r + CX[i] + CY[i] * sy + CZ[i] * sz] = fi[i] - omega * (fi[i] - psi) + src;
+                const float even = omega * (K1 + 4.5f * na * (2.f * cu * cb - cb * cb)) + (K2 + 9.f * ks * cb * ca);
+                const float odd = 3.f * (omega * na * cu + ks * ca);
+                long long dp = CX[i] + CY[i] * sy + CZ[i] * sz;       // i: +c, i + 1: -c
+                long long dm = -dp;
+                if (CX[i] > 0) { dp += wxp; dm += wxm; }
+                if (CX[i] < 0) { dp += wxm; dm += wxp; }
+                if (CY[i] > 0) { dp += wyp; dm += wym; }
+                if (CY[i] < 0) { dp += wym; dm += wyp; }
+                if (CZ[i] > 0) { dp += wzp; dm += wzm; }
+                if (CZ[i] < 0) { dp += wzm; dm += wzp; }
+                o[i * N + dp] = om1 * fi[i] + WQ[i] * (even + odd);
+                o[(i + 1) * N + dm] = om1 * fi[i + 1] + WQ[i] * (even - odd);
             }
         } else {
-            // faces: periodic wrap or halfway bounce-back; compact loop
 #pragma unroll 1
             for (int i = 0; i < MLBI_Q; ++i) {
                 const int cx = CXv(i), cy = CYv(i), cz = CZv(i);
@@ -950,13 +1122,13 @@ __global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, c
                 const float src = w * ks * (3.f * ca + 9.f * cb * ca - 1.5f * trS);
                 const float fv = __ldg(fa + i * N);
                 const float post = fv - omega * (fv - psi) + src;
-                const long long q = neighbour(p, L.x, L.y, L.z, cx, cy, cz);
+                const long long q = neighbour(p, x, y, z, cx, cy, cz);
                 if (q >= 0) {
                     oa[i * N + q] = post;
                 } else {
                     const int ax = p.wall_axis;
                     const int cax = ax == 0 ? cx : (ax == 1 ? cy : cz);
-                    const int xa = ax == 0 ? L.x : (ax == 1 ? L.y : L.z);
+                    const int xa = ax == 0 ? x : (ax == 1 ? y : z);
                     const float *uw = (xa + cax < 0) ? p.wall_lo : p.wall_hi;
                     const float cuw = cx * uw[0] + cy * uw[1] + cz * uw[2];
                     oa[opposite(i) * N + r] = post - 6.f * w * na * cuw;
@@ -964,6 +1136,25 @@ __global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, c
             }
         }
     }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, const float *__restrict__ fin,
+                                                          float *__restrict__ fout, const float4 *__restrict__ mom,
+                                                          const float4 *__restrict__ accf)
+{
+    Loc L;
+    if (!locate(p, L)) return;
+    const long long N = p.N, r = L.r;
+    Centre<S> c;
+    load_centre<S>(p, mom, r, c);
+    float acc[S][3];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 v = accf[a * N + r];
+        acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z;
+    }
+    collide_push<S>(p, L.x, L.y, L.z, r, c, acc, fin, fout);
 }
 
 // ------------------------------------------------------------------ initial populations
@@ -1010,21 +1201,14 @@ __global__ void __launch_bounds__(kBlock) k_export_moments(mlbi_params p, const 
     const long long N = p.N;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
-        double n[MLBI_MAXS], j[MLBI_MAXS][3], rho = 0.0, m[3] = {0.0, 0.0, 0.0};
         for (int a = 0; a < p.S; ++a) {
-            float4 v = mom[a * N + r];
+            const float4 v = mom[a * N + r];
             if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w)) atomicOr(flags, MLBI_FLAG_NAN);
-            n[a] = (double)p.nref[a] + (double)v.x;
-            j[a][0] = v.y; j[a][1] = v.z; j[a][2] = v.w;
-            rho += n[a];
-            for (int q = 0; q < 3; ++q) m[q] += j[a][q];
-        }
-        for (int a = 0; a < p.S; ++a) {
-            if (nout) nout[a * N + r] = n[a];
+            if (nout) nout[a * N + r] = (double)p.nref[a] + (double)v.x;
             if (uout) {
-                const bool ok = n[a] > (double)kTinyDensity;
-                for (int q = 0; q < 3; ++q)
-                    uout[(a * 3 + q) * N + r] = ok ? j[a][q] / n[a] : (rho > 0.0 ? m[q] / rho : 0.0);
+                uout[(a * 3 + 0) * N + r] = v.y;
+                uout[(a * 3 + 1) * N + r] = v.z;
+                uout[(a * 3 + 2) * N + r] = v.w;
             }
         }
     }
@@ -1057,10 +1241,11 @@ __global__ void __launch_bounds__(kBlock) k_conservation(mlbi_params p, const fl
         for (int a = 0; a < p.S; ++a) {
             float4 v = mom[a * p.N + r];
             bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+            const double n = (double)p.nref[a] + (double)v.x;
             acc[a] += (double)v.x;
-            acc[p.S + 0] += (double)v.y;
-            acc[p.S + 1] += (double)v.z;
-            acc[p.S + 2] += (double)v.w;
+            acc[p.S + 0] += n * (double)v.y;
+            acc[p.S + 1] += n * (double)v.z;
+            acc[p.S + 2] += n * (double)v.w;
         }
     }
     if (bad) atomicOr(flags, MLBI_FLAG_NAN);
@@ -1093,7 +1278,13 @@ __global__ void k_conservation_final(mlbi_params p, const double *__restrict__ p
 
 cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
 {
-    k_moments<<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom);
+    switch (p.S) {
+    case 1: k_moments<1><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
+    case 2: k_moments<2><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
+    case 3: k_moments<3><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
+    case 4: k_moments<4><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
