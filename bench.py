@@ -75,6 +75,52 @@ def algorithmic_bytes(kernel, S, npairs, has_fext=False, local_g=True):
     return table.get(kernel)
 
 
+def shell_points(sigma):
+    """sum over ordered species pairs of |S_ab|, the lattice points with
+    (sigma_ab - 1/2)^2 <= |d|^2 < (sigma_ab + 1/2)^2 (the contact shells)."""
+    tot = 0
+    for sa in sigma:
+        for sb in sigma:
+            s = 0.5 * (sa + sb)
+            R = int(math.ceil(s + 0.5)) + 1
+            for dz in range(-R, R + 1):
+                for dy in range(-R, R + 1):
+                    for dx in range(-R, R + 1):
+                        q = dx * dx + dy * dy + dz * dz
+                        if q > 0 and (s - 0.5) ** 2 <= q < (s + 0.5) ** 2:
+                            tot += 1
+    return tot
+
+
+# algorithmic FP32 operations per (ordered pair, contact-shell point):
+#   pass 1: pair value (2), hard core (7), velocity exchange (15), friction tensor (12)
+#   pass 2: pair value (2), velocity exchange (16)
+FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18}
+
+
+def fp32_peak_tflops(sm_mhz=2070.0):
+    """152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def committed_traffic(kernel, size):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; None otherwise."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1105_3634_gb300", "csrc", "mlb_kernels.cu")
+    prof = os.path.join(ROOT, "profiles", "step_kernels_binary128_ncu.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(prof):
+            if line.startswith("bench-traffic:"):
+                kv = dict(t.split("=", 1) for t in line.split()[1:])
+                if kv["kernel"] == kernel and int(kv["size"]) == size and kv["kernel_source_sha256_16"] == sha:
+                    return float(kv["bytes_per_launch"])
+    except Exception:
+        return None
+    return None
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -232,9 +278,11 @@ def run_mlb(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "what": "mlb_set_fields from pinned host n, K x (mlb_step(1) + mlb_conservation), mlb_get_moments"}
 
-    # roofline of the dominant kernel (largest device time in the timed region)
+    # roofline of the dominant kernel (largest device time in the timed region):
+    # the stencil passes are bound by FP32 issue, the others by HBM
     npairs = S * (S + 1) // 2
     peak, peak_kind = measured_peak_hbm()
+    pts = shell_points(lat.sigma)
     kernels = {}
     for name, (ms, cnt) in prof.items():
         if cnt == 0:
@@ -242,17 +290,30 @@ def run_mlb(args, rank, world, local_rank):
         per_launch_ms = ms / cnt
         bss = algorithmic_bytes(name, S, npairs)
         b = bss * S * N if bss is not None else None
-        kernels[name] = {"launches": cnt, "ms_total": ms, "ms_per_launch": per_launch_ms,
-                         "share": ms / sum(v[0] for v in prof.values()),
-                         "algorithmic_bytes_per_launch": b,
-                         "achieved_gbs": (b / (per_launch_ms * 1e-3) / 1e9) if b is not None else None}
-    top = max((k for k in kernels if kernels[k]["achieved_gbs"] is not None), key=lambda k: kernels[k]["ms_total"])
-    roof = {"kernel": top, "bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak,
-            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "unit": "GB/s", "frac": kernels[top]["achieved_gbs"] / peak, "traffic": None}
+        k = {"launches": cnt, "ms_total": ms, "ms_per_launch": per_launch_ms,
+             "share": ms / sum(v[0] for v in prof.values()), "algorithmic_bytes_per_launch": b,
+             "achieved_gbs": (b / (per_launch_ms * 1e-3) / 1e9) if b is not None else None}
+        if name in FLOPS_PER_SHELL_POINT:
+            fl = FLOPS_PER_SHELL_POINT[name] * pts * N
+            k["algorithmic_flops_per_launch"] = fl
+            k["achieved_tflops"] = fl / (per_launch_ms * 1e-3) / 1e12
+        kernels[name] = k
+    top = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if "achieved_tflops" in kernels[top]:
+        fpk = fp32_peak_tflops(sm_mhz)
+        roof = {"kernel": top, "bound": "alu", "achieved": kernels[top]["achieved_tflops"], "peak": fpk,
+                "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (no measured FP32 peak)",
+                "unit": "TFLOP/s", "frac": kernels[top]["achieved_tflops"] / fpk,
+                "traffic": committed_traffic(top, args.size)}
+    else:
+        roof = {"kernel": top, "bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "unit": "GB/s", "frac": kernels[top]["achieved_gbs"] / peak,
+                "traffic": committed_traffic(top, args.size)}
     step_bytes = 184.0 * S * N
     step_roof = {"bytes_per_species_site": 184, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
-                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak}
+                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "peak_gbs": peak}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
