@@ -1,0 +1,83 @@
+"""Mutual diffusion measured on the GPU (the experiment of Sec. V, Eq.
+perturba): a small concentration wave decays at exp(-D q^2 t); the decay
+rate fitted on the GPU must equal the rate of the slowest concentration mode
+of the linear operator L(q) (equal, to 1e-7, to the oracle's evolution) to
+well within 1 %, and for equal diameters that D is the paper's Eq. dab."""
+import math
+
+import numpy as np
+import pytest
+
+import linear_model as LM
+from paper_1105_3634_gb300 import workloads as W
+from test_physics_pins import eq_dab
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_3634_gb300 import build
+    build.build()
+    from paper_1105_3634_gb300 import mlb
+    return mlb
+
+
+def concentration_mode(lat, n0, q):
+    """Eigenvalue and left eigenvector of the slowest concentration mode of L(q)."""
+    Lm, Dn, Dj = LM.operator(lat, n0, np.array([q, 0.0, 0.0]))
+    ev, V = np.linalg.eig(Lm)
+    Vinv = np.linalg.inv(V)
+    best = None
+    for i in range(len(ev)):
+        w = abs((Dn @ V[:, i])[0] * n0[1] - (Dn @ V[:, i])[1] * n0[0]) / np.linalg.norm(V[:, i])
+        if abs(ev[i]) > 0.5 and (best is None or w > best[0]):
+            best = (w, i)
+    return ev[best[1]], Vinv[best[1]]
+
+
+def fitted_D(mlbmod, lat, n0, amp, t0, t1, every):
+    """Decay rate of the concentration mode on the GPU: the Fourier amplitude of
+    every population at q = 2 pi / L_x, projected onto the mode's left
+    eigenvector (the linear model's velocity order), fitted over [t0, t1]."""
+    L = lat.shape[0]
+    q = 2 * math.pi / L
+    S = lat.nspecies
+    lam, left = concentration_mode(lat, n0, q)
+    cm, _ = LM.d3q19()
+    cg, wg = mlbmod.velocity_set()
+    perm = [int(np.where((cm == v).all(1))[0][0]) for v in cg]     # gpu index -> model index
+    n = W.sine_wave(lat, n0, amp, axis=0, wavelength=L)
+    sim = mlbmod.Simulation(lat)
+    sim.set_fields(n)
+    ph = np.exp(-1j * q * W.coordinate(lat, 0)) / lat.nsites
+    ts, amps = [], []
+    sim.step(t0)
+    for t in range(t0, t1 + 1, every):
+        f, nref, _ = sim.populations()
+        xg = f.astype(np.float64) @ ph                  # [S][19] Fourier amplitudes (deviation parts)
+        x = np.zeros(S * 19, complex)
+        for a in range(S):
+            for i in range(19):
+                x[a * 19 + perm[i]] = xg[a, i]          # w_i n_ref has no q != 0 component
+        ts.append(t)
+        amps.append(abs(left @ x))
+        sim.step(every)
+    sim.close()
+    slope = np.polyfit(np.array(ts, float), np.log(np.array(amps)), 1)[0]
+    return -slope / q ** 2, -math.log(abs(lam)) / q ** 2
+
+
+@pytest.mark.parametrize("sigma,packing,shape", [
+    ([1.0, 1.5], 0.2, (64, 4, 4)),      # the benchmark physics (tiled kernels)
+    ([4.0, 4.0], 0.3, (64, 6, 6)),      # equal diameters (global-memory kernels)
+])
+def test_gpu_mutual_diffusion(gpu, sigma, packing, shape):
+    lat = W.Lattice(shape=shape, sigma=sigma, tau=1.0)
+    n0 = W.densities_from_packing(packing, sigma, [0.5, 0.5])
+    D_gpu, D_lin = fitted_D(gpu, lat, n0, 1e-3, 100, 1100, 50)
+    print(f"sigma={sigma} packing={packing}: D_gpu={D_gpu:.6f} D_discrete={D_lin:.6f} Eq.dab={eq_dab(sigma, n0):.6f}")
+    assert abs(D_gpu - D_lin) < 1e-3 * D_lin
