@@ -39,21 +39,31 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mlb", "reference"], default="mlb")
-    ap.add_argument("--size", type=int, default=256, help="cubic lattice extent")
+    ap.add_argument("--size", type=int, default=None, help="cubic lattice extent (default: the workload's)")
+    ap.add_argument("--workload", choices=["binary", "attraction"], default="binary",
+                    help="binary: sigma 1/1.5 packing 0.2 (256^3); attraction: sigma 2/3, eps kT/2 tails, "
+                         "packing 0.3, 1%% noise (128^3)")
     ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample extent for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload(size):
+DEFAULT_SIZE = {"binary": 256, "attraction": 128}
+
+
+def workload(size, kind="binary"):
     from paper_1105_3634_gb300 import workloads as W
-    lat, n = W.binary_config1((size, size, size))
-    return lat, n
+    if kind == "attraction":
+        return W.binary_attraction((size, size, size))
+    return W.binary_config1((size, size, size))
 
 
-def config_dict(size):
-    return {"workload": f"binary hard spheres sigma=(1,1.5), packing 0.2, tau=1, 5% sine wave, {size}^3 periodic D3Q19",
+def config_dict(size, kind="binary"):
+    desc = {"binary": "binary hard spheres sigma=(1,1.5), packing 0.2, tau=1, 5% sine wave",
+            "attraction": "binary sigma=(2,3), attractive tails -eps(sigma/r)^6 to 2.5 sigma, eps=kT/2, "
+                          "packing 0.3, 1% noise, tau=1"}[kind]
+    return {"workload": f"{desc}, {size}^3 periodic D3Q19",
             "grid": [size, size, size], "species": 2, "lattice": "D3Q19", "precision": "FP32 populations",
             "force_scheme": "semi-implicit half-force shift",
             "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (2 * 19 * 4 * size ** 3 / 1e9),
@@ -71,6 +81,7 @@ def algorithmic_bytes(kernel, S, npairs, has_fext=False, local_g=True):
         "k_pass1": 16 + g + 12 + 16 + (12 if has_fext else 0),    # moments, g read; frest, p* write
         "k_pass2": 16 + g + 12 + 16 + 12,                          # moments, g, frest, p* read; acc write
         "k_collide": 76 + 16 + 12 + 76,                            # f, moments, acc read; f write
+        "k_attraction": 4 + 12,                                     # n - n_ref read; G write
     }
     return table.get(kernel)
 
@@ -92,10 +103,33 @@ def shell_points(sigma):
     return tot
 
 
-# algorithmic FP32 operations per (ordered pair, contact-shell point):
+def attraction_points(lat):
+    """sum over ordered species pairs with eps_ab != 0 of |A_ab|, the lattice
+    points with sigma_ab <= |d| <= lambda_c sigma_ab."""
+    tot = 0
+    S = len(lat.sigma)
+    for a in range(S):
+        for b in range(S):
+            if lat.eps[a][b] == 0.0:
+                continue
+            s = 0.5 * (lat.sigma[a] + lat.sigma[b])
+            rc = lat.lambda_c[a][b] * s
+            R = int(math.ceil(rc)) + 1
+            for dz in range(-R, R + 1):
+                for dy in range(-R, R + 1):
+                    for dx in range(-R, R + 1):
+                        q = dx * dx + dy * dy + dz * dz
+                        if q > 0 and s * s <= q <= rc * rc:
+                            tot += 1
+    return tot
+
+
+# algorithmic FP32 operations per (ordered pair, stencil point):
 #   pass 1: pair value (2), hard core (7), velocity exchange (15), friction tensor (12)
 #   pass 2: pair value (2), velocity exchange (16)
+#   attraction: one vector multiply-add (6)
 FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18}
+FLOPS_PER_ATTRACTION_POINT = 6
 
 
 def fp32_peak_tflops(sm_mhz=2070.0):
@@ -119,6 +153,21 @@ def committed_traffic(kernel, size):
     except Exception:
         return None
     return None
+
+
+def reduce_max(value, dist=None, device=None):
+    """Maximum of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, nspecies, nsites, steps, seconds):
+    """Whole-job MLUPS per species: every rank advances its own replica."""
+    return world * nspecies * nsites * steps / seconds / 1e6
 
 
 def measured_peak_hbm():
@@ -181,11 +230,11 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ cpu baseline (oracle)
-def cpu_baseline(size, steps=2):
+def cpu_baseline(size, kind="binary", steps=2):
     import numpy as np
     import oracle
     oracle.build()
-    lat, n = workload(size)
+    lat, n = workload(size, kind)
     f = oracle.init(lat, n)
     oracle.step(lat, f, 1)                    # warm (page-in, thread pool)
     t0 = time.perf_counter()
@@ -210,7 +259,7 @@ def run_mlb(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    lat, n = workload(args.size)
+    lat, n = workload(args.size, args.workload)
     S, N = lat.nspecies, lat.nsites
     stream = torch.cuda.Stream(device=dev)
     sim = mlb.Simulation(lat, stream=stream)
@@ -242,12 +291,9 @@ def run_mlb(args, rank, world, local_rank):
     ms_total = t_start.elapsed_time(t_end)
     prof = sim.profile_read()
     sim.profile(False)
-    if dist:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    value = world * S * N * args.steps / (ms_total * 1e-3) / 1e6
+    value = job_value(world, S, N, args.steps, ms_total * 1e-3)
 
     # end to end through the C ABI with host buffers: upload the fields, then
     # every step a device->host read of the conservation sums (the monitored
@@ -267,14 +313,10 @@ def run_mlb(args, rank, world, local_rank):
             sim.step(1)
             sim.conservation()
         sim.moments(n_out, u_out)
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = reduce_max(time.perf_counter() - t0, dist, dev)
         h2d = nh.nbytes / args.steps
         d2h = (S + 3) * 8 + (n_out.nbytes + u_out.nbytes) / args.steps
-        e2e = {"value": world * S * N * args.steps / dt / 1e6, "unit": UNIT,
+        e2e = {"value": job_value(world, S, N, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "what": "mlb_set_fields from pinned host n, K x (mlb_step(1) + mlb_conservation), mlb_get_moments"}
 
@@ -293,8 +335,12 @@ def run_mlb(args, rank, world, local_rank):
         k = {"launches": cnt, "ms_total": ms, "ms_per_launch": per_launch_ms,
              "share": ms / sum(v[0] for v in prof.values()), "algorithmic_bytes_per_launch": b,
              "achieved_gbs": (b / (per_launch_ms * 1e-3) / 1e9) if b is not None else None}
+        fl = None
         if name in FLOPS_PER_SHELL_POINT:
             fl = FLOPS_PER_SHELL_POINT[name] * pts * N
+        elif name == "k_attraction":
+            fl = FLOPS_PER_ATTRACTION_POINT * attraction_points(lat) * N
+        if fl is not None:
             k["algorithmic_flops_per_launch"] = fl
             k["achieved_tflops"] = fl / (per_launch_ms * 1e-3) / 1e12
         kernels[name] = k
@@ -318,12 +364,12 @@ def run_mlb(args, rank, world, local_rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sine-wave mixture)",
-           "config": config_dict(args.size), "roofline": roof, "step_roofline": step_roof,
+           "config": config_dict(args.size, args.workload), "roofline": roof, "step_roofline": step_roof,
            "kernels": kernels, "gpu_launches": sim.launches_per_step() * args.steps * 1,
            "mlups": value / S, "clocks": clk, "e2e": e2e}
     sim.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample if args.workload == "binary" else 48, args.workload)
     if dist:
         dist.destroy_process_group()
     return out
@@ -334,8 +380,8 @@ def run_reference(args):
     time step of a bounded sample (96^3) of the same workload."""
     import oracle
     oracle.build()
-    size = min(args.size, 96)
-    lat, n = workload(size)
+    size = min(args.size, 96 if args.workload == "binary" else 40)
+    lat, n = workload(size, args.workload)
     f = oracle.init(lat, n)
     if args.warmup:
         oracle.step(lat, f, args.warmup)
@@ -348,13 +394,15 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded sine-wave mixture)", "config": config_dict(args.size),
+            "data": "synthetic (seeded sine-wave mixture)", "config": config_dict(args.size, args.workload),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 
 
 def main():
     args = parse_args()
+    if args.size is None:
+        args.size = DEFAULT_SIZE[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

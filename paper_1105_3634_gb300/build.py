@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmlb.so")
-SOURCES = ["mlb_api.cu", "mlb_kernels.cu", "mlb_noalloc.cu"]
+SOURCES = ["mlb_api.cu", "mlb_kernels.cu", "mlb_passes.cu", "mlb_attraction.cu", "mlb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -38,7 +38,8 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    headers = [os.path.join(CSRC, "mlb_internal.h"), os.path.join(ROOT, "include", "mlb.h")]
+    headers = [os.path.join(CSRC, "mlb_internal.h"), os.path.join(CSRC, "mlb_device.cuh"),
+               os.path.join(ROOT, "include", "mlb.h")]
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     os.makedirs(BUILD, exist_ok=True)
     objs = [os.path.join(BUILD, os.path.splitext(s)[0] + ".o") for s in SOURCES]

@@ -112,6 +112,15 @@ mlb_status rebuild(mlb_ctx *c)
         }
     const int tile_r = shell_reach <= 2 ? shell_reach : 0;
     const int txh = 32 + 2 * tile_r;
+    // reach of the attraction regions (tiled attraction kernel if <= 8)
+    int attr_reach = 0;
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b)
+            if (!c->eps.empty() && c->eps[a * S + b] != 0.0)
+                attr_reach = std::max(attr_reach,
+                                      (int)std::floor(c->lambda_c[a * S + b] * 0.5 * (c->sigma[a] + c->sigma[b]) + 1e-9));
+    const int attr_r = (attr_reach >= 1 && attr_reach <= 8) ? attr_reach : 0;
+    int cur_txh = txh;                              // tile width the next entries are addressed in
     auto push = [&](int dx, int dy, int dz, double vx, double vy, double vz, int mask) {
         mlbi_entry e0, e1;
         e0.x = (float)vx; e0.y = (float)vy; e0.z = (float)vz;
@@ -119,7 +128,7 @@ mlb_status rebuild(mlb_ctx *c)
         std::memcpy(&e0.w, &packed, sizeof(int));
         long long lin = dx + nx * dy + nxy * dz;
         if (lin >= (1ll << 31) || lin <= -(1ll << 31)) lin_overflow = true;
-        int lin32 = (int)lin, tileoff = dx + txh * dy, dzz = dz;
+        int lin32 = (int)lin, tileoff = dx + cur_txh * dy, dzz = dz;
         std::memcpy(&e1.x, &lin32, sizeof(int));
         std::memcpy(&e1.y, &mask, sizeof(int));
         std::memcpy(&e1.z, &tileoff, sizeof(int));
@@ -175,6 +184,7 @@ mlb_status rebuild(mlb_ctx *c)
             pr.g_ref = (float)bmcsl(c->sigma[a], c->sigma[b], xi2, xi3);
             // attraction: K(d) = 6 eps sigma^6 d / |d|^8 on sigma <= |d| <= lambda_c sigma
             pr.attr_start = count();
+            cur_txh = 32 + 2 * attr_r;                  // attraction entries: the attraction tile
             const double e = c->eps.empty() ? 0.0 : c->eps[a * S + b];
             if (e != 0.0) {
                 attraction = true;
@@ -192,6 +202,7 @@ mlb_status rebuild(mlb_ctx *c)
                         }
             }
             pr.attr_count = count() - pr.attr_start;
+            cur_txh = txh;
             p.pair_index[a][b] = p.pair_index[b][a] = np;
             ++np;
         }
@@ -230,6 +241,7 @@ mlb_status rebuild(mlb_ctx *c)
     for (int g = 0; g < S; ++g)
         if (p.ball_count[g] != 1) p.local_g = 0;
     p.tile_r = tile_r;
+    p.attr_r = attraction ? attr_r : 0;
     p.zchunk = std::min(c->desc.nz, 16);
     // the 13 canonical half offsets of the 3x3x3 cube, in the order the kernels use:
     // (1,0,0); (-1,1,0), (0,1,0), (1,1,0); then dz = 1 with dy = -1, 0, 1 and dx = -1, 0, 1
@@ -281,8 +293,9 @@ mlb_status require_ready(mlb_ctx *c)
     return MLB_OK;
 }
 
-enum { K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_NKINDS = 5 };
-const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2", "k_collide"};
+enum { K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_ATTRACTION = 5, K_NKINDS = 6 };
+const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2", "k_collide",
+                                            "k_attraction"};
 
 // event pair around one launch when profiling
 struct Timed {
@@ -318,6 +331,10 @@ mlb_status forces(mlb_ctx *c)
     } else {
         { Timed t(c, K_MOMENTS); MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream)); }
         { Timed t(c, K_GFIELD); MLB_CUDA(c, mlbi_launch_gfield(c->p, c->b, c->stream)); }
+    }
+    if (c->p.attr_r) {
+        Timed t(c, K_ATTRACTION);
+        MLB_CUDA(c, mlbi_launch_attraction(c->p, c->b, c->stream));
     }
     { Timed t(c, K_PASS1); MLB_CUDA(c, mlbi_launch_pass1(c->p, c->b, c->stream)); }
     return MLB_OK;
@@ -432,7 +449,7 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     size_t sz_part = align256(sizeof(double) * MLBI_RED_BLOCKS * (S + 3));
     size_t sz_sums = align256(sizeof(double) * (S + 3));
     size_t sz_flags = 256;
-    c->slab_bytes = 2 * sz_f + 6 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
+    c->slab_bytes = 2 * sz_f + 7 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
     if (d->dev_alloc) {
         c->slab = d->dev_alloc(c->slab_bytes, d->alloc_user);
         if (!c->slab) {
@@ -457,6 +474,7 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     c->b.pst = (float4 *)q; q += sz_v4;
     c->b.du = (float4 *)q; q += sz_v4;
     c->b.acc = (float4 *)q; q += sz_v4;
+    c->b.attr = (float4 *)q; q += sz_v4;
     c->b.fext = (float4 *)q; q += sz_v4;
     c->b.dg = (float *)q; q += sz_dg;
     c->b.table = (const mlbi_entry *)q; q += sz_tab;
@@ -620,7 +638,7 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;
-    return (c->p.local_g ? 1 : 2) + 3;
+    return (c->p.local_g ? 1 : 2) + 3 + (c->p.attr_r ? 1 : 0);
 }
 
 const char *mlb_kernel_name(int32_t k)

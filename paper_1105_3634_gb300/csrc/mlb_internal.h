@@ -61,6 +61,7 @@ struct mlbi_params {
     int local_g;                     // every smoothing ball is the single site
     int tile_r;                      // reach of the union shells if the tiled kernels serve it (1, 2), else 0
     int cube_mask[MLBI_MAXP];        // tile_r == 1: bit k set when half offset k of the 3x3x3 cube is in S_ab
+    int attr_r;                      // reach of the attraction if the tiled attraction kernel serves it (1..8), else 0
     int zchunk;                      // planes per block of the tiled kernels
     int pair_index[MLBI_MAXS][MLBI_MAXS];
     mlbi_pair pair[MLBI_MAXP];
@@ -76,6 +77,7 @@ struct mlbi_buffers {
     float4 *pst;                     // [S][N]  pass 1 -> 2: (n - n_ref, j + n du)
     float4 *du;                      // [S][N]  pass 1 -> 2: du (drag-only mode)
     float4 *acc;                     // [S][N]  pass 2 -> collide: acceleration
+    float4 *attr;                    // [S][N]  attraction G^a (tiled attraction kernel -> pass 1)
     float4 *fext;                    // [S][N]  external force (if any)
     const mlbi_entry *table;         // stencil entries
     double *stage;                   // [S*4*N] FP64 staging for host transfers
@@ -92,6 +94,7 @@ struct mlbi_buffers {
 cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
+cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s);
 cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
