@@ -112,7 +112,7 @@ mlb_status rebuild(mlb_ctx *c)
         }
     const int tile_r = shell_reach <= 2 ? shell_reach : 0;
     const int txh = 32 + 2 * tile_r;
-    // reach of the attraction regions (tiled attraction kernel if <= 8)
+    // reach of the attraction regions (column attraction kernel if <= 8)
     int attr_reach = 0;
     for (int a = 0; a < S; ++a)
         for (int b = 0; b < S; ++b)
@@ -120,7 +120,6 @@ mlb_status rebuild(mlb_ctx *c)
                 attr_reach = std::max(attr_reach,
                                       (int)std::floor(c->lambda_c[a * S + b] * 0.5 * (c->sigma[a] + c->sigma[b]) + 1e-9));
     const int attr_r = (attr_reach >= 1 && attr_reach <= 8) ? attr_reach : 0;
-    int cur_txh = txh;                              // tile width the next entries are addressed in
     auto push = [&](int dx, int dy, int dz, double vx, double vy, double vz, int mask) {
         mlbi_entry e0, e1;
         e0.x = (float)vx; e0.y = (float)vy; e0.z = (float)vz;
@@ -128,7 +127,7 @@ mlb_status rebuild(mlb_ctx *c)
         std::memcpy(&e0.w, &packed, sizeof(int));
         long long lin = dx + nx * dy + nxy * dz;
         if (lin >= (1ll << 31) || lin <= -(1ll << 31)) lin_overflow = true;
-        int lin32 = (int)lin, tileoff = dx + cur_txh * dy, dzz = dz;
+        int lin32 = (int)lin, tileoff = dx + txh * dy, dzz = dz;
         std::memcpy(&e1.x, &lin32, sizeof(int));
         std::memcpy(&e1.y, &mask, sizeof(int));
         std::memcpy(&e1.z, &tileoff, sizeof(int));
@@ -183,11 +182,11 @@ mlb_status rebuild(mlb_ctx *c)
             pr.h = (float)(c->sigma[a] * c->sigma[b] / (c->sigma[a] + c->sigma[b]));
             pr.g_ref = (float)bmcsl(c->sigma[a], c->sigma[b], xi2, xi3);
             // attraction: K(d) = 6 eps sigma^6 d / |d|^8 on sigma <= |d| <= lambda_c sigma
+            // (one entry per point of the half region, for reaches the column form does not serve)
             pr.attr_start = count();
-            cur_txh = 32 + 2 * attr_r;                  // attraction entries: the attraction tile
             const double e = c->eps.empty() ? 0.0 : c->eps[a * S + b];
-            if (e != 0.0) {
-                attraction = true;
+            if (e != 0.0) attraction = true;
+            if (e != 0.0 && !attr_r) {
                 const double rc = c->lambda_c[a * S + b] * sab;
                 const int Rc = (int)std::ceil(rc) + 1;
                 const double s6 = std::pow(sab, 6.0);
@@ -202,7 +201,6 @@ mlb_status rebuild(mlb_ctx *c)
                         }
             }
             pr.attr_count = count() - pr.attr_start;
-            cur_txh = txh;
             p.pair_index[a][b] = p.pair_index[b][a] = np;
             ++np;
         }
@@ -225,10 +223,68 @@ mlb_status rebuild(mlb_ctx *c)
                 }
         p.ushell_count[b] = count() - p.ushell_start[b];
     }
+    if (attraction) maxoff = std::max(maxoff, attr_reach);
+    // column form of the attraction: the region sigma_ab <= |d| <= lambda_c sigma_ab
+    // cut into columns (dx, dy) of the half plane; per column and pair the
+    // profile k(dz) = 6 eps sigma^6 / |d|^8 (zero off the region) and dz k(dz)
+    p.acol_start = p.acol_count = p.aw_start = 0;
+    if (attraction && attr_r) {
+        struct Col { int dx, dy, E; };
+        std::vector<Col> cols;
+        auto rc_of = [&](int a, int b) { return c->lambda_c[a * S + b] * 0.5 * (c->sigma[a] + c->sigma[b]); };
+        for (int dy = 0; dy <= attr_r; ++dy)
+            for (int dx = -attr_r; dx <= attr_r; ++dx) {
+                if (dy == 0 && dx < 0) continue;                    // half plane, (0, 0) kept
+                int E = -1;
+                for (int a = 0; a < S; ++a)
+                    for (int b = a; b < S; ++b) {
+                        if (c->eps[a * S + b] == 0.0) continue;
+                        const double rc = rc_of(a, b), sab = 0.5 * (c->sigma[a] + c->sigma[b]);
+                        for (int dz = 0; dz <= attr_r; ++dz) {
+                            const double q = (double)(dx * dx + dy * dy + dz * dz);
+                            if (q > 0.0 && q >= sab * sab && q <= rc * rc) E = std::max(E, dz);
+                        }
+                    }
+                if (E >= 0) cols.push_back({dx, dy, E});
+            }
+        p.acol_start = (int)tab.size();                            // float4 index
+        for (const Col &k : cols) {
+            mlbi_entry e;
+            std::memcpy(&e.x, &k.dx, sizeof(int));
+            std::memcpy(&e.y, &k.dy, sizeof(int));
+            std::memcpy(&e.z, &k.E, sizeof(int));
+            e.w = 0.f;
+            tab.push_back(e);
+        }
+        p.acol_count = (int)cols.size();
+        std::vector<float> w;                                       // (k, dz k) pairs
+        for (const Col &k : cols)
+            for (int a = 0; a < S; ++a)
+                for (int b = a; b < S; ++b) {
+                    const double e = c->eps[a * S + b], sab = 0.5 * (c->sigma[a] + c->sigma[b]);
+                    const double rc = rc_of(a, b), s6 = std::pow(sab, 6.0);
+                    for (int dz = 0; dz <= attr_r; ++dz) {
+                        const double q = (double)(k.dx * k.dx + k.dy * k.dy + dz * dz);
+                        const bool in = e != 0.0 && q > 0.0 && q >= sab * sab && q <= rc * rc;
+                        const double kk = in ? 6.0 * e * s6 / (q * q * q * q) : 0.0;
+                        // the (0, 0) column pairs with itself: its +-dz sum counts each point twice
+                        const double half = (k.dx == 0 && k.dy == 0) ? 0.5 : 1.0;
+                        w.push_back((float)kk);
+                        w.push_back((float)(half * dz * kk));
+                    }
+                }
+        while (w.size() % 4) w.push_back(0.f);
+        p.aw_start = (int)tab.size();
+        for (size_t i = 0; i < w.size(); i += 4) {
+            mlbi_entry e;
+            e.x = w[i]; e.y = w[i + 1]; e.z = w[i + 2]; e.w = w[i + 3];
+            tab.push_back(e);
+        }
+    }
     if (lin_overflow) return fail(c, MLB_EINVAL, "stencil offsets exceed 32-bit linear offsets on this lattice");
-    if (count() > kTableCap)
-        return fail(c, MLB_EINVAL, "stencil tables need %d entries, capacity is %d (reduce sigma or lambda_c)",
-                    count(), kTableCap);
+    if (tab.size() > 2 * (size_t)kTableCap)
+        return fail(c, MLB_EINVAL, "stencil tables need %d float4, capacity is %d (reduce sigma or lambda_c)",
+                    (int)tab.size(), 2 * kTableCap);
     const int L[3] = {c->desc.nx, c->desc.ny, c->desc.nz};
     for (int ax = 0; ax < 3; ++ax)
         if (ax != c->desc.wall_axis && L[ax] <= maxoff)

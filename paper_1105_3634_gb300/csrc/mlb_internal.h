@@ -61,7 +61,12 @@ struct mlbi_params {
     int local_g;                     // every smoothing ball is the single site
     int tile_r;                      // reach of the union shells if the tiled kernels serve it (1, 2), else 0
     int cube_mask[MLBI_MAXP];        // tile_r == 1: bit k set when half offset k of the 3x3x3 cube is in S_ab
-    int attr_r;                      // reach of the attraction if the tiled attraction kernel serves it (1..8), else 0
+    int attr_r;                      // reach of the attraction if the column attraction kernel serves it (1..8), else 0
+    // column form of the attraction (attr_r > 0): acol_count columns (dx, dy) of the
+    // half plane, one float4 each at table[acol_start] = (dx, dy, E, 0) as int bits,
+    // E the largest |dz| any pair reaches on the column; their weights are float2
+    // (k, dz k) per (column, pair, dz = 0..attr_r) at ((float2 *)(table + aw_start))
+    int acol_start, acol_count, aw_start;
     int zchunk;                      // planes per block of the tiled kernels
     int pair_index[MLBI_MAXS][MLBI_MAXS];
     mlbi_pair pair[MLBI_MAXP];
@@ -77,7 +82,7 @@ struct mlbi_buffers {
     float4 *pst;                     // [S][N]  pass 1 -> 2: (n - n_ref, j + n du)
     float4 *du;                      // [S][N]  pass 1 -> 2: du (drag-only mode)
     float4 *acc;                     // [S][N]  pass 2 -> collide: acceleration
-    float4 *attr;                    // [S][N]  attraction G^a (tiled attraction kernel -> pass 1)
+    float4 *attr;                    // [S][N]  attraction G^a (column attraction kernel -> pass 1)
     float4 *fext;                    // [S][N]  external force (if any)
     const mlbi_entry *table;         // stencil entries
     double *stage;                   // [S*4*N] FP64 staging for host transfers

@@ -100,6 +100,51 @@ def test_attraction_ragged_box(gpu, orc):
     assert ok(w), w
 
 
+# attraction in isolation: the acceleration is linear in the mean field G^a at
+# fixed densities and velocities, so a(eps) - a(eps = 0) is the attraction's
+# share on both sides; cases span every species-group shape of the column
+# kernel (S = 1..4), the reach tiers 3, 5, 7, 8, walls on x and z, ragged tiles
+ATTRACTION_CASES = {
+    "S1_reach3": dict(shape=(20, 12, 11), sigma=[2.0], lam=1.5, wall=-1),
+    "S2_reach7_zwalls": dict(shape=(36, 10, 19), sigma=[2.0, 3.0], lam=2.5, wall=2),
+    "S3_reach5_xwalls": dict(shape=(22, 13, 12), sigma=[1.5, 2.0, 2.5], lam=2.0, wall=0, zero=(0, 2)),
+    "S4_reach8": dict(shape=(19, 18, 17), sigma=[1.0, 1.5, 2.0, 2.5], lam=3.4, wall=-1),
+}
+
+
+def attraction_lattices(case):
+    S = len(case["sigma"])
+    eps = [[0.3 * W.KT_LATTICE * (1.0 + 0.1 * (a + b)) for b in range(S)] for a in range(S)]
+    if "zero" in case:
+        a, b = case["zero"]
+        eps[a][b] = eps[b][a] = 0.0
+    lam = [[case["lam"]] * S for _ in range(S)]
+    mk = lambda e: W.Lattice(shape=case["shape"], sigma=case["sigma"], eps=e, lambda_c=lam,
+                             wall_axis=case["wall"])
+    return mk(eps), mk(None)
+
+
+@pytest.mark.parametrize("name", sorted(ATTRACTION_CASES))
+def test_attraction_field_isolated(gpu, orc, name):
+    lat, lat0 = attraction_lattices(ATTRACTION_CASES[name])
+    n0 = W.densities_from_packing(0.25, lat.sigma, [1.0 / lat.nspecies] * lat.nspecies)
+    n = W.noise(lat, n0, 0.05, seed=31)
+    u = W.random_velocities(lat, 0.01, seed=32)
+    j = n[:, None, :] * u
+    got = []
+    for L in (lat, lat0):
+        sim = gpu.Simulation(L)
+        sim.set_fields(n, u)
+        got.append(sim.acceleration())
+        sim.close()
+    g_gpu = got[0] - got[1]
+    g_orc = orc.accel(lat, n, j) - orc.accel(lat0, n, j)
+    assert np.abs(g_orc).max() > 1e-6
+    # FP32 accumulation over ~1e3 - 1e4 region points of 5% deviations
+    assert rel(g_gpu, g_orc) < 2e-4, (name, rel(g_gpu, g_orc))
+    assert rel2(g_gpu, g_orc) < 5e-5, (name, rel2(g_gpu, g_orc))
+
+
 def test_taylor_channel_three_species_walls(gpu, orc):
     """Two solvents sigma = 2, 2.5 and a dilute solute sigma = 3 between
     walls moving at -U, +U (halfway bounce-back), 40x16x10, 150 steps."""
