@@ -127,7 +127,7 @@ def attraction_points(lat):
 # algorithmic FP32 operations per (ordered pair, stencil point):
 #   pass 1: pair value (2), hard core (7), velocity exchange (15), friction tensor (12)
 #   pass 2: pair value (2), velocity exchange (16)
-#   attraction: one vector multiply-add (6)
+#   attraction: one 3-vector multiply-add per point of the full region (6)
 FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18}
 FLOPS_PER_ATTRACTION_POINT = 6
 
@@ -137,18 +137,35 @@ def fp32_peak_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def committed_traffic(kernel, size):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; None otherwise."""
+KERNEL_SOURCE = {"k_pass1": "mlb_passes.cu", "k_pass2": "mlb_passes.cu", "k_attraction": "mlb_attraction.cu"}
+
+
+def kernel_source_sha(kernel):
+    """First 16 hex digits of the SHA-256 of the kernel's translation unit and
+    the internal headers it includes."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1105_3634_gb300", "csrc", "mlb_kernels.cu")
-    prof = os.path.join(ROOT, "profiles", "step_kernels_binary128_ncu.md")
+    csrc = os.path.join(ROOT, "paper_1105_3634_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in (KERNEL_SOURCE.get(kernel, "mlb_kernels.cu"), "mlb_device.cuh", "mlb_internal.h"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, size, kind="binary"):
+    """DRAM bytes per launch from a committed ncu summary under profiles/
+    (a line `bench-traffic: kernel=... workload=... size=... bytes_per_launch=...
+    kernel_source_sha256_16=...`), if it was taken on the current kernel
+    source; None otherwise."""
+    pdir = os.path.join(ROOT, "profiles")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        for line in open(prof):
-            if line.startswith("bench-traffic:"):
+        sha = kernel_source_sha(kernel)
+        for name in sorted(os.listdir(pdir)):
+            for line in open(os.path.join(pdir, name)):
+                if not line.startswith("bench-traffic:"):
+                    continue
                 kv = dict(t.split("=", 1) for t in line.split()[1:])
-                if kv["kernel"] == kernel and int(kv["size"]) == size and kv["kernel_source_sha256_16"] == sha:
+                if (kv.get("kernel") == kernel and kv.get("workload", "binary") == kind
+                        and int(kv.get("size", -1)) == size and kv.get("kernel_source_sha256_16") == sha):
                     return float(kv["bytes_per_launch"])
     except Exception:
         return None
@@ -340,6 +357,8 @@ def run_mlb(args, rank, world, local_rank):
             fl = FLOPS_PER_SHELL_POINT[name] * pts * N
         elif name == "k_attraction":
             fl = FLOPS_PER_ATTRACTION_POINT * attraction_points(lat) * N
+            k["flops_note"] = ("direct lattice sum, one 3-vector FMA per region point; the column kernel "
+                               "executes about 1.25 FP32 flops per point through K(-d) = -K(d)")
         if fl is not None:
             k["algorithmic_flops_per_launch"] = fl
             k["achieved_tflops"] = fl / (per_launch_ms * 1e-3) / 1e12
@@ -351,12 +370,12 @@ def run_mlb(args, rank, world, local_rank):
         roof = {"kernel": top, "bound": "alu", "achieved": kernels[top]["achieved_tflops"], "peak": fpk,
                 "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (no measured FP32 peak)",
                 "unit": "TFLOP/s", "frac": kernels[top]["achieved_tflops"] / fpk,
-                "traffic": committed_traffic(top, args.size)}
+                "traffic": committed_traffic(top, args.size, args.workload)}
     else:
         roof = {"kernel": top, "bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "unit": "GB/s", "frac": kernels[top]["achieved_gbs"] / peak,
-                "traffic": committed_traffic(top, args.size)}
+                "traffic": committed_traffic(top, args.size, args.workload)}
     step_bytes = 184.0 * S * N
     step_roof = {"bytes_per_species_site": 184, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
                  "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "peak_gbs": peak}

@@ -505,7 +505,7 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     size_t sz_part = align256(sizeof(double) * MLBI_RED_BLOCKS * (S + 3));
     size_t sz_sums = align256(sizeof(double) * (S + 3));
     size_t sz_flags = 256;
-    c->slab_bytes = 2 * sz_f + 7 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
+    c->slab_bytes = 2 * sz_f + 6 * sz_v4 + sz_dg + sz_tab + sz_stage + sz_part + sz_sums + sz_flags;
     if (d->dev_alloc) {
         c->slab = d->dev_alloc(c->slab_bytes, d->alloc_user);
         if (!c->slab) {
@@ -528,7 +528,6 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     c->b.mom = (float4 *)q; q += sz_v4;
     c->b.frest = (float4 *)q; q += sz_v4;
     c->b.pst = (float4 *)q; q += sz_v4;
-    c->b.du = (float4 *)q; q += sz_v4;
     c->b.acc = (float4 *)q; q += sz_v4;
     c->b.attr = (float4 *)q; q += sz_v4;
     c->b.fext = (float4 *)q; q += sz_v4;

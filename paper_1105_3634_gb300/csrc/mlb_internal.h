@@ -1,5 +1,6 @@
 // mlb_internal.h -- definitions shared by the C-ABI runtime (mlb_api.cu) and
-// the sm_103a kernels (mlb_kernels.cu).  Not part of the public ABI.
+// the sm_103a kernel units (mlb_kernels.cu, mlb_pass1.cu, mlb_pass2.cu,
+// mlb_attraction.cu).  Not part of the public ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -76,11 +77,10 @@ struct mlbi_params {
 // Device buffers of one context (all carved from one allocation).
 struct mlbi_buffers {
     float *f[2];                     // [S][19][N] populations minus w_i n_ref
-    float4 *mom;                     // [S][N]  (dn, jx, jy, jz), dn = n - n_ref
+    float4 *mom;                     // [S][N]  (dn, ux, uy, uz), dn = n - n_ref
     float *dg;                       // [npairs][N]  g_ab - g_ref_ab
-    float4 *frest;                   // [S][N]  pass 1 -> 2: F^hc + G + F_ext - Gamma du
-    float4 *pst;                     // [S][N]  pass 1 -> 2: (n - n_ref, j + n du)
-    float4 *du;                      // [S][N]  pass 1 -> 2: du (drag-only mode)
+    float4 *frest;                   // [S][N]  pass 1 -> 2: F^hc + G + F_ext
+    float4 *pst;                     // [S][N]  pass 1 -> 2: (n - n_ref, u* = u + du)
     float4 *acc;                     // [S][N]  pass 2 -> collide: acceleration
     float4 *attr;                    // [S][N]  attraction G^a (column attraction kernel -> pass 1)
     float4 *fext;                    // [S][N]  external force (if any)
@@ -95,7 +95,7 @@ struct mlbi_buffers {
 #define MLBI_FLAG_XI3 1u
 #define MLBI_FLAG_NAN 2u
 
-// kernel launchers (mlb_kernels.cu); each returns cudaGetLastError()
+// kernel launchers (one per kernel unit); each returns cudaGetLastError()
 cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);

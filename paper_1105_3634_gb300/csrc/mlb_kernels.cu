@@ -5,8 +5,8 @@
 //   f[a][i][r]  FP32 populations minus w_i n_ref^a      (76 B per species-site)
 //   mom[a][r]   float4 (n - n_ref, u_x, u_y, u_z)        (16 B per species-site)
 //   dg[p][r]    g_ab - g_ab(reference densities)          (per unordered pair)
-//   frest[a][r] F^hc + G + F_ext - Gamma du               (pass 1 -> pass 2)
-//   pst[a][r]   (n - n_ref, u + du)                       (pass 1 -> pass 2)
+//   frest[a][r] F^hc + G + F_ext                          (pass 1 -> pass 2)
+//   pst[a][r]   (n - n_ref, u* = u + du)                  (pass 1 -> pass 2)
 //
 // One step (all launches on one stream):
 //   k_moments        f -> mom                                    (Eq. colonna)
@@ -15,7 +15,7 @@
 //   k_pass1          mom, dg -> frest, pst: hard core + attraction  (Eqs. potmeanforce, gammaab,
 //                    + velocity exchange at u, then the one-sweep    viscousforce)
 //                    half-step predictor
-//   k_pass2          velocity exchange at u + du -> acc
+//   k_pass2          velocity exchange at u* = u + du -> acc
 //   k_collide        collision toward psi_perp at u + a/2 with      (Eqs. evolution, prefactor)
 //                    (1 - omega/2) forcing, push streaming /
 //                    halfway bounce-back

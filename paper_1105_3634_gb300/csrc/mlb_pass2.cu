@@ -1,0 +1,296 @@
+// mlb_pass2.cu -- pass 2 of a time step on sm_103a: the velocity exchange
+// (Eqs. gammaab, viscousforce) at the predicted velocities u* of pass 1,
+// completed to the acceleration a^a = frest^a + sum_points s sd (masses 1).
+// Same three variants as pass 1: global memory, tile with the stencil table
+// (reach 2), compile-time 3x3x3 cube (reach 1).
+#include "mlb_passes.cuh"
+
+namespace {
+
+// centre velocities u*^a(r) from pass 1's (n - n_ref, u*) field
+template <int S>
+__device__ __forceinline__ void centre_ustar(const mlbi_params &p, const float4 *__restrict__ pst, long long r,
+                                             float (&us)[S][3])
+{
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 v = pst[a * p.N + r];
+        us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void store_acc(const mlbi_params &p, long long r, const float (&acc)[S][3],
+                                          float4 *__restrict__ acc_f, double *__restrict__ acc_out)
+{
+    const long long N = p.N;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        if (acc_out) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc_out[(a * 3 + q) * N + r] = (double)acc[a][q];
+        } else {
+            acc_f[a * N + r] = make_float4(acc[a][0], acc[a][1], acc[a][2], 0.f);
+        }
+    }
+}
+
+// a^a = frest^a + vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 n^b(r+d) (u*^b(r+d) - u*^a(r))]
+// (drag only: -wn s.(u*^a - u*^b)(r) per point)
+template <int S, bool DRAG, bool INTERIOR>
+__device__ __forceinline__ void pass2_shells(const mlbi_params &p, const Loc &L, const PairW<S> &w,
+                                             const float (&us)[S][3], const float4 *__restrict__ pst,
+                                             const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
+                                             float (&acc)[S][3])
+{
+    const long long N = p.N;
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
+        const float4 *fb = pst + b * N;
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+            const float4 e0 = __ldg(&tab[2 * k]);
+            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const int mask = __float_as_int(e1.y);
+            const Nb P = fetch_nb<INTERIOR>(p, L, e0, e1, 1, fb, p.nref[b]);
+            const Nb M = fetch_nb<INTERIOR>(p, L, e0, e1, -1, fb, p.nref[b]);
+            const float sx = e0.x, sy = e0.y, sz = e0.z;
+            const float jp = DRAG ? 0.f : sx * P.u0 + sy * P.u1 + sz * P.u2;
+            const float jm = DRAG ? 0.f : sx * M.u0 + sy * M.u1 + sz * M.u2;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                if (!(mask & (1 << a))) continue;
+                const int q = pair_of(a, b, S);
+                const float su = DRAG ? 0.f : sx * us[a][0] + sy * us[a][1] + sz * us[a][2];
+                const float *dgq = dg + q * N;
+                const float dgp = (INTERIOR || P.q >= 0) ? dgq[P.q] : 0.f;
+                const float dgm = (INTERIOR || M.q >= 0) ? dgq[M.q] : 0.f;
+                const float sdu = DRAG ? sx * (us[a][0] - us[b][0]) + sy * (us[a][1] - us[b][1]) +
+                                             sz * (us[a][2] - us[b][2])
+                                       : 0.f;
+                const float sd = pass2_point<DRAG>(P.n, M.n, jp - su, jm - su, dgp, dgm, w.kp[q],
+                                                   0.5f * p.pair[q].vx_pre, sdu);
+                acc[a][0] = fmaf(sx, sd, acc[a][0]);
+                acc[a][1] = fmaf(sy, sd, acc[a][1]);
+                acc[a][2] = fmaf(sz, sd, acc[a][2]);
+            }
+        }
+    }
+}
+
+template <int S, bool DRAG>
+__global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const float *__restrict__ dg,
+                                                     const mlbi_entry *__restrict__ tab,
+                                                     const float4 *__restrict__ frest,
+                                                     const float4 *__restrict__ pst, float4 *__restrict__ acc_f,
+                                                     double *__restrict__ acc_out)
+{
+    constexpr int NP = S * (S + 1) / 2;
+    Loc L;
+    if (!locate(p, L)) return;
+    const long long N = p.N, r = L.r;
+    float dgc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) dgc[q] = dg[q * N + r];
+    PairW<S> w;
+    pair_weights<S>(p, dgc, w);
+    float us[S][3];
+    centre_ustar<S>(p, pst, r, us);
+    float acc[S][3];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 fr = frest[a * N + r];
+        acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
+    }
+    if (L.interior) pass2_shells<S, DRAG, true>(p, L, w, us, pst, dg, tab, acc);
+    else pass2_shells<S, DRAG, false>(p, L, w, us, pst, dg, tab, acc);
+    store_acc<S>(p, r, acc, acc_f, acc_out);
+}
+
+// ------------------------------------------------------------------ tiled variants
+template <int S, int R, bool DRAG>
+__device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
+                                                  const float4 *sf, const float *sg, int kz, int cidx,
+                                                  const PairW<S> &w, const float (&us)[S][3], float (&acc)[S][3])
+{
+    using T = Tile<S, R>;
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        const float nr = p.nref[b];
+        const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+            const float4 e0 = __ldg(&tab[2 * k]);
+            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
+            const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);
+            const float4 vp = sf[sp * S * T::PLANE + b * T::PLANE + cidx + off];
+            const float4 vm = sf[sm * S * T::PLANE + b * T::PLANE + cidx - off];
+            const float np = nr + vp.x, nm = nr + vm.x;
+            const float sx = e0.x, sy = e0.y, sz = e0.z;
+            const float jp = DRAG ? 0.f : sx * vp.y + sy * vp.z + sz * vp.w;
+            const float jm = DRAG ? 0.f : sx * vm.y + sy * vm.z + sz * vm.w;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                if (!(mask & (1 << a))) continue;
+                const int q = pair_of(a, b, S);
+                const float su = DRAG ? 0.f : sx * us[a][0] + sy * us[a][1] + sz * us[a][2];
+                const float dgp = sg[sp * T::NP * T::PLANE + q * T::PLANE + cidx + off];
+                const float dgm = sg[sm * T::NP * T::PLANE + q * T::PLANE + cidx - off];
+                const float sdu = DRAG ? sx * (us[a][0] - us[b][0]) + sy * (us[a][1] - us[b][1]) +
+                                             sz * (us[a][2] - us[b][2])
+                                       : 0.f;
+                const float sd = pass2_point<DRAG>(np, nm, jp - su, jm - su, dgp, dgm, w.kp[q],
+                                                   0.5f * p.pair[q].vx_pre, sdu);
+                acc[a][0] = fmaf(sx, sd, acc[a][0]);
+                acc[a][1] = fmaf(sy, sd, acc[a][1]);
+                acc[a][2] = fmaf(sz, sd, acc[a][2]);
+            }
+        }
+    }
+}
+
+// reach 1 by offset class (see pass1_cube_class)
+template <int S, bool DRAG, int CL>
+__device__ __forceinline__ void pass2_cube_class(const mlbi_params &p, const float4 *sf, const float *sg, int b,
+                                                 const int (&f)[3], const int (&g)[3], const PairW<S> &w,
+                                                 const float (&us)[S][3], float (&acc)[S][3])
+{
+    using T = Tile<S, 1>;
+    constexpr float il = cls_il(CL);
+    bool has[S];
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        has[a] = (p.cube_mask[pair_of(a, b, S)] >> cls_bit(CL)) & 1;
+        any |= has[a];
+    }
+    if (!any) return;
+    const float nr = p.nref[b];
+    static_for<0, cls_n(CL)>([&](auto I) {
+        constexpr int k = cls_k(CL, decltype(I)::value);
+        constexpr int off = cube_kx(k) + T::TXH * cube_ky(k), dz = cube_kz(k);
+        const float4 vp = sf[f[1 + dz] + b * T::PLANE + off];
+        const float4 vm = sf[f[1 - dz] + b * T::PLANE - off];
+        const float np = nr + vp.x, nm = nr + vm.x;
+        const float jp = DRAG ? 0.f : cube_dot<k>(il, vp.y, vp.z, vp.w);
+        const float jm = DRAG ? 0.f : cube_dot<k>(il, vm.y, vm.z, vm.w);
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            if (!has[a]) continue;
+            const int q = pair_of(a, b, S);
+            const float dgp = sg[g[1 + dz] + q * T::PLANE + off];
+            const float dgm = sg[g[1 - dz] + q * T::PLANE - off];
+            const float sdu = DRAG ? cube_dot<k>(il, us[a][0] - us[b][0], us[a][1] - us[b][1], us[a][2] - us[b][2])
+                                   : 0.f;
+            const float su = DRAG ? 0.f : cube_dot<k>(il, us[a][0], us[a][1], us[a][2]);
+            const float sd = pass2_point<DRAG>(np, nm, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre,
+                                               sdu);
+            cube_add<k>(il, sd, acc[a]);
+        }
+    });
+}
+
+template <int S, bool DRAG>
+__device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *sf, const float *sg, int kz, int cidx,
+                                           const PairW<S> &w, const float (&us)[S][3], float (&acc)[S][3])
+{
+    using T = Tile<S, 1>;
+    const int f[3] = {ring(kz - 1, T::NSLOT) * S * T::PLANE + cidx, ring(kz, T::NSLOT) * S * T::PLANE + cidx,
+                      ring(kz + 1, T::NSLOT) * S * T::PLANE + cidx};
+    const int g[3] = {ring(kz - 1, T::NSLOT) * T::NP * T::PLANE + cidx, ring(kz, T::NSLOT) * T::NP * T::PLANE + cidx,
+                      ring(kz + 1, T::NSLOT) * T::NP * T::PLANE + cidx};
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        pass2_cube_class<S, DRAG, 0>(p, sf, sg, b, f, g, w, us, acc);
+        pass2_cube_class<S, DRAG, 1>(p, sf, sg, b, f, g, w, us, acc);
+        pass2_cube_class<S, DRAG, 2>(p, sf, sg, b, f, g, w, us, acc);
+    }
+}
+
+template <int S, int R, bool DRAG>
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const mlbi_params p, const float *__restrict__ dg,
+                                                              const mlbi_entry *__restrict__ tab,
+                                                              const float4 *__restrict__ frest,
+                                                              const float4 *__restrict__ pst,
+                                                              float4 *__restrict__ acc_f, double *__restrict__ acc_out)
+{
+    using T = Tile<S, R>;
+    extern __shared__ float4 smem[];
+    float4 *sf = smem;
+    float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);
+    const long long N = p.N;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int z1 = min(z0 + p.zchunk, p.nz);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool active = x < p.nx && y < p.ny;
+    const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    int xy[T::J];
+    stage_sites<S, R>(p, x0, y0, xy);
+    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    cp_async_commit();
+    for (int z = z0; z < z1; ++z) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int kz = z - z0 + R;
+        if (z + 1 < z1) {
+            stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
+            cp_async_commit();
+        }
+        if (!active) continue;
+        const int cs = ring(kz, T::NSLOT);
+        const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
+        float dgc[T::NP];
+#pragma unroll
+        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[cs * T::NP * T::PLANE + q * T::PLANE + cidx];
+        PairW<S> w;
+        pair_weights<S>(p, dgc, w);
+        float us[S][3];
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const float4 v = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
+            us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
+        }
+        float acc[S][3];
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const float4 fr = frest[a * N + r];
+            acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
+        }
+        if constexpr (R == 1) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
+        else pass2_tile_shells<S, R, DRAG>(p, tab, sf, sg, kz, cidx, w, us, acc);
+        store_acc<S>(p, r, acc, acc_f, acc_out);
+    }
+}
+
+template <int S, int R, bool DRAG>
+cudaError_t launch_pass2_tiled(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
+{
+    using T = Tile<S, R>;
+    auto k = k_pass2_tiled<S, R, DRAG>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+    if (e != cudaSuccess) return e;
+    const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
+                 (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+    k<<<g, dim3(kBX, kBY), T::bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
+    return cudaGetLastError();
+}
+
+template <int S, bool DRAG>
+cudaError_t launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
+{
+    if (p.tile_r == 1) return launch_pass2_tiled<S, 1, DRAG>(p, b, acc_out, s);
+    if (p.tile_r == 2) return launch_pass2_tiled<S, 2, DRAG>(p, b, acc_out, s);
+    k_pass2<S, DRAG><<<tiled_grid(p), dim3(kBX, kBY), 0, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
+{
+    if (p.drag_only) { MLBI_DISPATCH_S(return launch_pass2<SS, true>(p, b, acc_out, s)); }
+    MLBI_DISPATCH_S(return launch_pass2<SS, false>(p, b, acc_out, s));
+    return cudaErrorInvalidValue;
+}

@@ -1,0 +1,253 @@
+// mlb_passes.cuh -- device code shared by the two force passes of a time step
+// (mlb_pass1.cu, mlb_pass2.cu): per-site pair weights, the arithmetic of one
+// +-d pair of a contact shell, the shared-memory z-marching tiles and the
+// compile-time offsets of the 3x3x3 cube.  Internal header.
+#pragma once
+
+#include "mlb_internal.h"
+#include "mlb_device.cuh"
+
+#include <type_traits>
+
+namespace {
+
+// ------------------------------------------------------------------ pair weights
+// The midpoint contact value of Eqs. potmeanforce and gammaab between r and
+// r + d is (g(r) + g(r+d))/2 = B + dg(r+d)/2 with B = g_ref + dg(r)/2 and
+// dg = g - g_ref.  Per site and pair (a, b):
+//   exchange weight  vx_ab (g(r) + g(r+d))/2 = kp + k1 dg(r+d),  kp = vx_ab B,  k1 = vx_ab / 2
+//   hard core        -hc_ab [(g(r)+g(r+d))/2 n(r+d) - (g(r)+g(r-d))/2 n(r-d)]
+//                    = h (n(r+d) - n(r-d)) + c (n(r+d) dg(r+d) - n(r-d) dg(r-d)),
+//                    h = -hc_ab B,  c = -hc_ab / 2,
+// with n(r+d) - n(r-d) formed from the deviations n - n_ref (exact to rounding).
+template <int S>
+struct PairW {
+    static constexpr int NP = S * (S + 1) / 2;
+    float kp[NP], h[NP];
+};
+
+template <int S>
+__device__ __forceinline__ void pair_weights(const mlbi_params &p, const float *dgc, PairW<S> &w)
+{
+#pragma unroll
+    for (int q = 0; q < PairW<S>::NP; ++q) {
+        const float B = fmaf(0.5f, dgc[q], p.pair[q].g_ref);
+        w.kp[q] = p.pair[q].vx_pre * B;
+        w.h[q] = -p.pair[q].hc_pre * B;
+    }
+}
+
+// ------------------------------------------------------------------ one +-d pair of a shell
+// Pass 1 (inputs at r +- d: n, the n - n_ref difference dd, dg, and
+// jp/jm = s.(u^b(r +- d) - u^a(r))):
+//   t  = hard-core projection on s (Eq. potmeanforce),
+//   wn = h+ + h-, the friction weight, h+- = weight(r +- d) n^b(r +- d),
+//   sd = h+ jp + h- jm, the exchange projection (Eqs. gammaab, viscousforce);
+//   drag only: sd = -wn s.(u^a - u^b)(r), with sdu = s.(u^a - u^b).
+template <bool DRAG>
+__device__ __forceinline__ void pass1_point(float np, float nm, float dd, float jp, float jm, float dgp, float dgm,
+                                            float kp, float k1, float h, float c, float sdu, float &t, float &sd,
+                                            float &wn)
+{
+    const float gp = fmaf(k1, dgp, kp), gm = fmaf(k1, dgm, kp);
+    t = fmaf(h, dd, c * fmaf(np, dgp, -nm * dgm));
+    const float hp = gp * np, hm = gm * nm;
+    wn = hp + hm;
+    sd = DRAG ? -wn * sdu : fmaf(hp, jp, hm * jm);
+}
+
+// Pass 2: the same exchange projection at u*, jp/jm = s.(u*^b(r +- d) - u*^a(r))
+// (drag only: sdu = s.(u*^a - u*^b)(r)).
+template <bool DRAG>
+__device__ __forceinline__ float pass2_point(float np, float nm, float jp, float jm, float dgp, float dgm, float kp,
+                                             float k1, float sdu)
+{
+    const float gp = fmaf(k1, dgp, kp), gm = fmaf(k1, dgm, kp);
+    const float hp = gp * np, hm = gm * nm;
+    return DRAG ? -(hp + hm) * sdu : fmaf(hp, jp, hm * jm);
+}
+
+// accumulate one point with a unit vector s given at run time
+__device__ __forceinline__ void add_pass1(float sx, float sy, float sz, float t, float sd, float wn, float (&hc)[3],
+                                          float (&fv)[3], float (&G)[6])
+{
+    hc[0] = fmaf(sx, t, hc[0]); hc[1] = fmaf(sy, t, hc[1]); hc[2] = fmaf(sz, t, hc[2]);
+    fv[0] = fmaf(sx, sd, fv[0]); fv[1] = fmaf(sy, sd, fv[1]); fv[2] = fmaf(sz, sd, fv[2]);
+    const float wx = wn * sx, wy = wn * sy;
+    G[0] = fmaf(wx, sx, G[0]); G[1] = fmaf(wy, sy, G[1]); G[2] = fmaf(wn * sz, sz, G[2]);
+    G[3] = fmaf(wx, sy, G[3]); G[4] = fmaf(wx, sz, G[4]); G[5] = fmaf(wy, sz, G[5]);
+}
+
+// ------------------------------------------------------------------ neighbours from global memory
+// species-b data at r + sign d (n = 0 and u = 0 beyond a wall): n, the
+// deviation n - n_ref, the velocity, and the site index (-1 beyond a wall)
+struct Nb {
+    float dn, n, u0, u1, u2;
+    long long q;
+};
+
+template <bool INTERIOR>
+__device__ __forceinline__ Nb fetch_nb(const mlbi_params &p, const Loc &L, const float4 &e0, const float4 &e1,
+                                       int sign, const float4 *__restrict__ fld, float nref)
+{
+    Nb o;
+    o.q = INTERIOR ? L.r + sign * (long long)__float_as_int(e1.x) : nbr(p, L, e0, e1, sign);
+    if (INTERIOR || o.q >= 0) {
+        const float4 v = fld[o.q];
+        o.dn = v.x; o.n = nref + v.x; o.u0 = v.y; o.u1 = v.z; o.u2 = v.w;
+    } else {
+        o.dn = -nref; o.n = 0.f; o.u0 = 0.f; o.u1 = 0.f; o.u2 = 0.f;
+    }
+    return o;
+}
+
+// ------------------------------------------------------------------ shared-memory tiles (z marching)
+// A block of 32 x 4 threads owns a 32 x 4 column of sites and marches up z
+// through `zchunk` planes.  The stencil field of every species (float4: the
+// moments in pass 1, (n - n_ref, u*) in pass 2) and the contact-value
+// deviations of every pair are staged in shared memory as a ring of planes
+// of (32 + 2R) x (4 + 2R) sites: 2R + 1 planes in use and one more being
+// filled by cp.async while the current plane is computed.  Every shell
+// neighbour is then read from shared memory.
+template <int S, int R>
+struct Tile {
+    static constexpr int TX = kBX, TY = kBY;
+    static constexpr int TXH = TX + 2 * R, TYH = TY + 2 * R, PLANE = TXH * TYH;
+    static constexpr int NSLOT = 2 * R + 2;
+    static constexpr int NP = S * (S + 1) / 2;
+    static constexpr int NT = kBX * kBY;
+    static constexpr int J = (PLANE + NT - 1) / NT;          // staging sites per thread and plane
+    static constexpr size_t bytes = (size_t)NSLOT * PLANE * (S * sizeof(float4) + NP * sizeof(float));
+};
+
+// (x, y) offsets x + nx y of this thread's staging sites, fixed while the
+// block marches up z; -1 beyond a wall
+template <int S, int R>
+__device__ __forceinline__ void stage_sites(const mlbi_params &p, int x0, int y0, int (&xy)[Tile<S, R>::J])
+{
+    using T = Tile<S, R>;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < T::J; ++j) {
+        const int idx = tid + j * T::NT;
+        const int hx = idx % T::TXH, hy = idx / T::TXH;
+        const int x = wrap_or_out(x0 - R + hx, p.nx, p.wall_axis == 0);
+        const int y = wrap_or_out(y0 - R + hy, p.ny, p.wall_axis == 1);
+        xy[j] = (x < 0 || y < 0) ? -1 : x + p.nx * y;
+    }
+}
+
+// plane index with one periodic wrap (|overhang| <= R < extent), or -1 beyond a wall
+__device__ __forceinline__ int wrap_plane(int c, int L, bool wall)
+{
+    if (wall) return (c < 0 || c >= L) ? -1 : c;
+    return c < 0 ? c + L : (c >= L ? c - L : c);
+}
+
+// Stage plane gz of the tile into ring slot `slot`.  Sites beyond a wall get
+// n = 0 (n - n_ref = -n_ref) and zero velocity; their dg is never used (every
+// term carries n(r+d) = 0) and is set to 0.
+template <int S, int R>
+__device__ __forceinline__ void stage_plane(const mlbi_params &p, const int (&xy)[Tile<S, R>::J], int gz, int slot,
+                                            const float4 *__restrict__ fld, const float *__restrict__ dg,
+                                            float4 *sf, float *sg)
+{
+    using T = Tile<S, R>;
+    const long long N = p.N;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const int z = wrap_plane(gz, p.nz, p.wall_axis == 2);
+    const long long zoff = (long long)p.nx * p.ny * z;
+#pragma unroll
+    for (int j = 0; j < T::J; ++j) {
+        const int idx = tid + j * T::NT;
+        if (j == T::J - 1 && idx >= T::PLANE) break;
+        float4 *df = sf + (size_t)slot * S * T::PLANE + idx;
+        float *dgs = sg + (size_t)slot * T::NP * T::PLANE + idx;
+        if (xy[j] < 0 || z < 0) {
+#pragma unroll
+            for (int b = 0; b < S; ++b) df[b * T::PLANE] = make_float4(-p.nref[b], 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < T::NP; ++q) dgs[q * T::PLANE] = 0.f;
+        } else {
+            const long long g = zoff + xy[j];
+#pragma unroll
+            for (int b = 0; b < S; ++b) cp_async16(df + b * T::PLANE, fld + b * N + g);
+#pragma unroll
+            for (int q = 0; q < T::NP; ++q) cp_async4(dgs + q * T::PLANE, dg + q * N + g);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ the 3x3x3 cube
+// The 13 canonical half offsets (first non-zero of (dz, dy, dx) positive).
+// With reach 1 every contact shell is a union of the three classes |d|^2 = 1
+// (axis), 2 (face diagonal), 3 (corner); the bit of class CL in cube_mask is
+// the bit of its first offset.  All compile-time: the class loops unroll and
+// the unit vectors become immediates.
+__host__ __device__ constexpr int cube_kx(int k) { return k == 0 || k == 3 || k == 6 || k == 9 || k == 12 ? 1 : (k == 1 || k == 4 || k == 7 || k == 10 ? -1 : 0); }
+__host__ __device__ constexpr int cube_ky(int k) { return k == 1 || k == 2 || k == 3 || k == 10 || k == 11 || k == 12 ? 1 : (k >= 4 && k <= 6 ? -1 : 0); }
+__host__ __device__ constexpr int cube_kz(int k) { return k >= 4 ? 1 : 0; }
+__host__ __device__ constexpr int cls_n(int cl) { return cl == 0 ? 3 : (cl == 1 ? 6 : 4); }
+__host__ __device__ constexpr int cls_bit(int cl) { return cl == 0 ? 0 : (cl == 1 ? 1 : 4); }
+__host__ __device__ constexpr int cls_k(int cl, int i)
+{
+    return cl == 0 ? (i == 0 ? 0 : (i == 1 ? 2 : 8)) : (cl == 1 ? 2 * i + 1 : (i < 2 ? 4 + 2 * i : 6 + 2 * i));
+}
+__host__ __device__ constexpr float cls_il(int cl)   // 1/|d|
+{
+    return cl == 0 ? 1.0f : (cl == 1 ? 0.70710678118654752f : 0.57735026918962576f);
+}
+
+// s . v for cube offset K (zero components drop out)
+template <int K>
+__device__ __forceinline__ float cube_dot(float il, float vx, float vy, float vz)
+{
+    float r = 0.f;
+    if constexpr (cube_kx(K) != 0) r = fmaf(cube_kx(K) * il, vx, r);
+    if constexpr (cube_ky(K) != 0) r = fmaf(cube_ky(K) * il, vy, r);
+    if constexpr (cube_kz(K) != 0) r = fmaf(cube_kz(K) * il, vz, r);
+    return r;
+}
+
+template <int K>
+__device__ __forceinline__ void cube_add(float il, float t, float (&v)[3])
+{
+    if constexpr (cube_kx(K) != 0) v[0] = fmaf(cube_kx(K) * il, t, v[0]);
+    if constexpr (cube_ky(K) != 0) v[1] = fmaf(cube_ky(K) * il, t, v[1]);
+    if constexpr (cube_kz(K) != 0) v[2] = fmaf(cube_kz(K) * il, t, v[2]);
+}
+
+// G += wn s s^T for cube offset K
+template <int K>
+__device__ __forceinline__ void cube_add_ss(float il, float wn, float (&G)[6])
+{
+    constexpr int X = cube_kx(K), Y = cube_ky(K), Z = cube_kz(K);
+    const float i2 = il * il;
+    if constexpr (X != 0) G[0] = fmaf(wn, i2, G[0]);
+    if constexpr (Y != 0) G[1] = fmaf(wn, i2, G[1]);
+    if constexpr (Z != 0) G[2] = fmaf(wn, i2, G[2]);
+    if constexpr (X * Y != 0) G[3] = fmaf(wn, X * Y * i2, G[3]);
+    if constexpr (X * Z != 0) G[4] = fmaf(wn, X * Z * i2, G[4]);
+    if constexpr (Y * Z != 0) G[5] = fmaf(wn, Y * Z * i2, G[5]);
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+}  // namespace
+
+#define MLBI_DISPATCH_S(...)                                                                       \
+    switch (p.S) {                                                                                 \
+    case 1: { constexpr int SS = 1; __VA_ARGS__; } break;                                          \
+    case 2: { constexpr int SS = 2; __VA_ARGS__; } break;                                          \
+    case 3: { constexpr int SS = 3; __VA_ARGS__; } break;                                          \
+    case 4: { constexpr int SS = 4; __VA_ARGS__; } break;                                          \
+    default: return cudaErrorInvalidValue;                                                         \
+    }
