@@ -62,6 +62,9 @@ typedef enum {
 /* flags */
 #define MLB_DRAG_ONLY       1u   /* partner velocity at r: Eq. gammaab alone, no viscous part */
 #define MLB_FORCE_EXPLICIT  2u   /* forward-Euler forcing at u (no half-force shift) */
+#define MLB_SPLIT_COLLIDE   4u   /* launch pass 2 and the collision separately (the acceleration
+                                    field is stored every step); default: one fused launch.
+                                    Both give bitwise-identical populations. */
 
 typedef struct {
     int32_t nx, ny, nz;          /* lattice extents, each >= 1 */

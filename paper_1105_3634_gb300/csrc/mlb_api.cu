@@ -349,9 +349,12 @@ mlb_status require_ready(mlb_ctx *c)
     return MLB_OK;
 }
 
-enum { K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_ATTRACTION = 5, K_NKINDS = 6 };
+enum {
+    K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_ATTRACTION = 5, K_PASS2_COLLIDE = 6,
+    K_NKINDS = 7
+};
 const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2", "k_collide",
-                                            "k_attraction"};
+                                            "k_attraction", "k_pass2_collide"};
 
 // event pair around one launch when profiling
 struct Timed {
@@ -399,8 +402,13 @@ mlb_status forces(mlb_ctx *c)
 // pass 2, collision and streaming of one step (after forces())
 mlb_status advance(mlb_ctx *c)
 {
-    { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
-    { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream)); }
+    if ((c->desc.flags & MLB_SPLIT_COLLIDE) || !c->p.tile_r) {
+        { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
+        { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream)); }
+    } else {
+        Timed t(c, K_PASS2_COLLIDE);
+        MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, c->b, c->cur, c->stream));
+    }
     return MLB_OK;
 }
 
@@ -455,7 +463,7 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     if (!(d->tau > 0.5) || !std::isfinite(d->tau)) return bad("tau must be finite and > 1/2");
     if (!(std::fabs(d->kT - kCs2) < 1e-12)) return bad("kT must be 1/3 (D3Q19 lattice units)");
     if (!(c->desc.kappa >= 0.0) || !std::isfinite(c->desc.kappa)) return bad("kappa must be >= 0");
-    if (d->flags & ~(MLB_DRAG_ONLY | MLB_FORCE_EXPLICIT)) return bad("unknown flag bits");
+    if (d->flags & ~(MLB_DRAG_ONLY | MLB_FORCE_EXPLICIT | MLB_SPLIT_COLLIDE)) return bad("unknown flag bits");
     if (d->wall_axis >= 0) {
         if (d->wall_u_lo[d->wall_axis] != 0.0 || d->wall_u_hi[d->wall_axis] != 0.0)
             return bad("wall velocities must be tangential to the wall");
@@ -693,7 +701,8 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;
-    return (c->p.local_g ? 1 : 2) + 3 + (c->p.attr_r ? 1 : 0);
+    const bool split = (c->desc.flags & MLB_SPLIT_COLLIDE) || !c->p.tile_r;
+    return (c->p.local_g ? 1 : 2) + (split ? 3 : 2) + (c->p.attr_r ? 1 : 0);
 }
 
 const char *mlb_kernel_name(int32_t k)

@@ -103,6 +103,9 @@ cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, 
 cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s);
 cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
+// pass 2 fused with the collision and streaming of f[cur] -> f[cur ^ 1] (no acceleration
+// stored); shared-memory tiled passes only (tile_r > 0), else cudaErrorInvalidValue
+cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_init(const mlbi_params &p, const mlbi_buffers &b, int cur, const double *n,
                              const double *u, cudaStream_t s);
 cudaError_t mlbi_launch_export_moments(const mlbi_params &p, const mlbi_buffers &b, double *n_out,

@@ -24,6 +24,7 @@
 // between neighbouring sites small and exact.
 #include "mlb_internal.h"
 #include "mlb_device.cuh"
+#include "mlb_collide.cuh"
 
 #include <math.h>
 
@@ -154,108 +155,6 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
     }
 }
 
-// ------------------------------------------------------------------ collide + stream
-// Collision toward psi_perp at u + a/2 (Eq. prefactor, Hermite-2) with the
-// forcing of Eq. evolution scaled by (1 - omega/2), then push streaming:
-// f(r + c_i) with periodic wrap by selects, or halfway bounce-back at walls.
-template <int S>
-__device__ __forceinline__ void collide_push(const mlbi_params &p, int x, int y, int z, long long r,
-                                             const Centre<S> &c, const float (&acc)[S][3],
-                                             const float *__restrict__ fin, float *__restrict__ fout)
-{
-    const long long N = p.N;
-    const float half = p.semi_implicit ? 0.5f : 0.f;
-    float ueq[S][3];
-    float ub[3] = {0.f, 0.f, 0.f}, rho = 0.f;
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            ueq[a][q] = c.u[a][q] + half * acc[a][q];
-            ub[q] += c.n[a] * ueq[a][q];
-        }
-        rho += c.n[a];
-    }
-    const float irho = rho > 0.f ? 1.f / rho : 0.f;
-    ub[0] *= irho; ub[1] *= irho; ub[2] *= irho;
-    const float ubub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-    const float omega = p.omega;
-    const long long sy = p.nx, sz = (long long)p.nx * p.ny;
-    // links that wrap around a periodic face move by -+ the extent; sites next
-    // to a wall take the compact bounce-back path
-    const bool wall_site = (p.wall_axis == 0 && (x == 0 || x == p.nx - 1)) ||
-                           (p.wall_axis == 1 && (y == 0 || y == p.ny - 1)) ||
-                           (p.wall_axis == 2 && (z == 0 || z == p.nz - 1));
-    const long long wxm = x == 0 ? p.nx : 0, wxp = x == p.nx - 1 ? -(long long)p.nx : 0;
-    const long long wym = y == 0 ? sz : 0, wyp = y == p.ny - 1 ? -sz : 0;
-    const long long wzm = z == 0 ? N : 0, wzp = z == p.nz - 1 ? -N : 0;
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const float na = c.n[a], dna = c.dn[a];
-        float *oa = fout + (long long)a * MLBI_Q * N;
-        const float *fa = fin + (long long)a * MLBI_Q * N + r;
-        float fi[MLBI_Q];
-#pragma unroll
-        for (int i = 0; i < MLBI_Q; ++i) fi[i] = __ldg(fa + i * N);
-        const float ua0 = ueq[a][0], ua1 = ueq[a][1], ua2 = ueq[a][2];
-        const float a0 = acc[a][0], a1 = acc[a][1], a2 = acc[a][2];
-        const float trM = 2.f * (ua0 * ub[0] + ua1 * ub[1] + ua2 * ub[2]) - ubub;   // tr(ua u + u ua - u u)
-        const float trS = 2.f * (ub[0] * a0 + ub[1] * a1 + ub[2] * a2);             // tr(u a + a u)
-        const float ks = p.src_scale * na;
-        if (!wall_site) {
-            // psi_perp and the forcing split into parts even and odd in c_i:
-            // direction i and its opposite share the even part and flip the odd one.
-            const float om1 = 1.f - omega;
-            const float K1 = dna - 1.5f * na * trM;          // even part of psi at c = 0
-            const float K2 = -1.5f * ks * trS;                // even part of the forcing at c = 0
-            float *o = oa + r;
-            o[0] = om1 * fi[0] + WQ[0] * (omega * K1 + K2);
-#pragma unroll
-            for (int i = 1; i < MLBI_Q; i += 2) {
-                const float cu = CX[i] * ua0 + CY[i] * ua1 + CZ[i] * ua2;
-                const float cb = CX[i] * ub[0] + CY[i] * ub[1] + CZ[i] * ub[2];
-                const float ca = CX[i] * a0 + CY[i] * a1 + CZ[i] * a2;
-                const float even = omega * (K1 + 4.5f * na * (2.f * cu * cb - cb * cb)) + (K2 + 9.f * ks * cb * ca);
-                const float odd = 3.f * (omega * na * cu + ks * ca);
-                long long dp = CX[i] + CY[i] * sy + CZ[i] * sz;       // i: +c, i + 1: -c
-                long long dm = -dp;
-                if (CX[i] > 0) { dp += wxp; dm += wxm; }
-                if (CX[i] < 0) { dp += wxm; dm += wxp; }
-                if (CY[i] > 0) { dp += wyp; dm += wym; }
-                if (CY[i] < 0) { dp += wym; dm += wyp; }
-                if (CZ[i] > 0) { dp += wzp; dm += wzm; }
-                if (CZ[i] < 0) { dp += wzm; dm += wzp; }
-                o[i * N + dp] = om1 * fi[i] + WQ[i] * (even + odd);
-                o[(i + 1) * N + dm] = om1 * fi[i + 1] + WQ[i] * (even - odd);
-            }
-        } else {
-#pragma unroll 1
-            for (int i = 0; i < MLBI_Q; ++i) {
-                const int cx = CXv(i), cy = CYv(i), cz = CZv(i);
-                const float w = WQv(i);
-                const float cu = cx * ua0 + cy * ua1 + cz * ua2;
-                const float cb = cx * ub[0] + cy * ub[1] + cz * ub[2];
-                const float ca = cx * a0 + cy * a1 + cz * a2;
-                const float psi = w * (dna + na * (3.f * cu + 4.5f * (2.f * cu * cb - cb * cb) - 1.5f * trM));
-                const float src = w * ks * (3.f * ca + 9.f * cb * ca - 1.5f * trS);
-                const float fv = __ldg(fa + i * N);
-                const float post = fv - omega * (fv - psi) + src;
-                const long long q = neighbour(p, x, y, z, cx, cy, cz);
-                if (q >= 0) {
-                    oa[i * N + q] = post;
-                } else {
-                    const int ax = p.wall_axis;
-                    const int cax = ax == 0 ? cx : (ax == 1 ? cy : cz);
-                    const int xa = ax == 0 ? x : (ax == 1 ? y : z);
-                    const float *uw = (xa + cax < 0) ? p.wall_lo : p.wall_hi;
-                    const float cuw = cx * uw[0] + cy * uw[1] + cz * uw[2];
-                    oa[opposite(i) * N + r] = post - 6.f * w * na * cuw;
-                }
-            }
-        }
-    }
-}
-
 template <int S>
 __global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, const float *__restrict__ fin,
                                                           float *__restrict__ fout, const float4 *__restrict__ mom,
@@ -272,7 +171,7 @@ __global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, c
         const float4 v = accf[a * N + r];
         acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z;
     }
-    collide_push<S>(p, L.x, L.y, L.z, r, c, acc, fin, fout);
+    collide_push<S>(p, L.x, L.y, L.z, r, c, acc, GlobalPops{fin + r, N}, fout);
 }
 
 // ------------------------------------------------------------------ initial populations

@@ -2,8 +2,12 @@
 // (Eqs. gammaab, viscousforce) at the predicted velocities u* of pass 1,
 // completed to the acceleration a^a = frest^a + sum_points s sd (masses 1).
 // Same three variants as pass 1: global memory, tile with the stencil table
-// (reach 2), compile-time 3x3x3 cube (reach 1).
+// (reach 2), compile-time 3x3x3 cube (reach 1).  The tiled variants also come
+// fused with the collision (k_pass2_collide): the acceleration is not stored,
+// the same thread collides and streams its site right away (the collision
+// needs only the site's own acceleration).
 #include "mlb_passes.cuh"
+#include "mlb_collide.cuh"
 
 namespace {
 
@@ -209,6 +213,34 @@ __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *s
     }
 }
 
+// the acceleration of the site at ring position kz of the tile (centre slot cs)
+template <int S, int R, bool DRAG>
+__device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *__restrict__ tab, const float4 *sf,
+                                           const float *sg, int kz, int cidx, const float4 *__restrict__ frest,
+                                           long long r, float (&acc)[S][3])
+{
+    using T = Tile<S, R>;
+    const int cs = ring(kz, T::NSLOT);
+    float dgc[T::NP];
+#pragma unroll
+    for (int q = 0; q < T::NP; ++q) dgc[q] = sg[cs * T::NP * T::PLANE + q * T::PLANE + cidx];
+    PairW<S> w;
+    pair_weights<S>(p, dgc, w);
+    float us[S][3];
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 v = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
+        us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float4 fr = frest[a * p.N + r];
+        acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
+    }
+    if constexpr (R == 1) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
+    else pass2_tile_shells<S, R, DRAG>(p, tab, sf, sg, kz, cidx, w, us, acc);
+}
+
 template <int S, int R, bool DRAG>
 __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const mlbi_params p, const float *__restrict__ dg,
                                                               const mlbi_entry *__restrict__ tab,
@@ -220,7 +252,6 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const
     extern __shared__ float4 smem[];
     float4 *sf = smem;
     float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);
-    const long long N = p.N;
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
@@ -239,29 +270,101 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const
             cp_async_commit();
         }
         if (!active) continue;
-        const int cs = ring(kz, T::NSLOT);
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
-        float dgc[T::NP];
-#pragma unroll
-        for (int q = 0; q < T::NP; ++q) dgc[q] = sg[cs * T::NP * T::PLANE + q * T::PLANE + cidx];
-        PairW<S> w;
-        pair_weights<S>(p, dgc, w);
-        float us[S][3];
-#pragma unroll
-        for (int a = 0; a < S; ++a) {
-            const float4 v = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
-            us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
-        }
         float acc[S][3];
-#pragma unroll
-        for (int a = 0; a < S; ++a) {
-            const float4 fr = frest[a * N + r];
-            acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
-        }
-        if constexpr (R == 1) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
-        else pass2_tile_shells<S, R, DRAG>(p, tab, sf, sg, kz, cidx, w, us, acc);
+        pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, frest, r, acc);
         store_acc<S>(p, r, acc, acc_f, acc_out);
     }
+}
+
+// ------------------------------------------------------------------ pass 2 fused with the collision
+// Per plane, each thread computes the acceleration of its site and at once
+// collides and streams the site.  The site's own populations and moments for
+// the next plane are prefetched by cp.async into a per-thread slot of shared
+// memory while this plane's shell sums run.  Two cp.async groups per plane,
+// committed by every thread (empty where there is nothing to copy): A = the
+// next halo plane of the stencil ring, F = the next populations.  Waiting for
+// "all but the newest group" therefore means "the ring" at the top of the
+// plane and "the populations" before the collision.
+template <int S, int R>
+struct FusedTile {
+    using T = Tile<S, R>;
+    static constexpr size_t pops_off = T::bytes;                                   // float [S*19][NT]
+    static constexpr size_t mom_off = pops_off + (size_t)S * MLBI_Q * T::NT * sizeof(float);   // float4 [S][NT]
+    static constexpr size_t bytes = mom_off + (size_t)S * T::NT * sizeof(float4);
+};
+
+template <int S>
+__device__ __forceinline__ void stage_site(const mlbi_params &p, long long r, int tid, int nt,
+                                           const float *__restrict__ fin, const float4 *__restrict__ mom,
+                                           float *sF, float4 *sM)
+{
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+#pragma unroll
+        for (int i = 0; i < MLBI_Q; ++i)
+            cp_async4(sF + (a * MLBI_Q + i) * nt + tid, fin + ((long long)a * MLBI_Q + i) * p.N + r);
+        cp_async16(sM + a * nt + tid, mom + a * p.N + r);
+    }
+}
+
+__device__ __forceinline__ void cp_async_wait_all_but_newest() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int S, int R, bool DRAG>
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(const mlbi_params p,
+                                                                            const float *__restrict__ dg,
+                                                                            const mlbi_entry *__restrict__ tab,
+                                                                            const float4 *__restrict__ frest,
+                                                                            const float4 *__restrict__ pst,
+                                                                            const float4 *__restrict__ mom,
+                                                                            const float *__restrict__ fin,
+                                                                            float *__restrict__ fout)
+{
+    using T = Tile<S, R>;
+    using F = FusedTile<S, R>;
+    extern __shared__ float4 smem[];
+    float4 *sf = smem;
+    float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);
+    float *sF = reinterpret_cast<float *>(reinterpret_cast<char *>(smem) + F::pops_off);
+    float4 *sM = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem) + F::mom_off);
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int z1 = min(z0 + p.zchunk, p.nz);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const bool active = x < p.nx && y < p.ny;
+    const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    const long long sxy = x + (long long)p.nx * y, nxy = (long long)p.nx * p.ny;
+    int xy[T::J];
+    stage_sites<S, R>(p, x0, y0, xy);
+    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    cp_async_commit();                                                  // A(z0)
+    if (active) stage_site<S>(p, sxy + nxy * z0, tid, T::NT, fin, mom, sF, sM);
+    cp_async_commit();                                                  // F(z0)
+    for (int z = z0; z < z1; ++z) {
+        cp_async_wait_all_but_newest();                                 // A(z) landed
+        __syncthreads();
+        const int kz = z - z0 + R;
+        if (z + 1 < z1) stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
+        cp_async_commit();                                              // A(z + 1)
+        const long long r = sxy + nxy * z;
+        float acc[S][3];
+        if (active) pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, frest, r, acc);
+        cp_async_wait_all_but_newest();                                 // F(z) landed (own slots only)
+        if (active) {
+            Centre<S> c;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                const float4 v = sM[a * T::NT + tid];
+                c.dn[a] = v.x;
+                c.n[a] = p.nref[a] + v.x;
+                c.u[a][0] = v.y; c.u[a][1] = v.z; c.u[a][2] = v.w;
+            }
+            collide_push<S>(p, x, y, z, r, c, acc, SharedPops{sF + tid, T::NT}, fout);
+            if (z + 1 < z1) stage_site<S>(p, r + nxy, tid, T::NT, fin, mom, sF, sM);
+        }
+        cp_async_commit();                                              // F(z + 1)
+    }
+    cp_async_wait_all();
 }
 
 template <int S, int R, bool DRAG>
@@ -286,11 +389,39 @@ cudaError_t launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *ac
     return cudaGetLastError();
 }
 
+template <int S, int R, bool DRAG>
+cudaError_t launch_pass2_collide_tiled(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+{
+    using F = FusedTile<S, R>;
+    auto k = k_pass2_collide<S, R, DRAG>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::bytes);
+    if (e != cudaSuccess) return e;
+    const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
+                 (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+    k<<<g, dim3(kBX, kBY), F::bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.mom, b.f[cur], b.f[cur ^ 1]);
+    return cudaGetLastError();
+}
+
+template <int S, bool DRAG>
+cudaError_t launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+{
+    if (p.tile_r == 1) return launch_pass2_collide_tiled<S, 1, DRAG>(p, b, cur, s);
+    if (p.tile_r == 2) return launch_pass2_collide_tiled<S, 2, DRAG>(p, b, cur, s);
+    return cudaErrorInvalidValue;          // the global-memory pass 2 is not fused
+}
+
 }  // namespace
 
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
 {
-    if (p.drag_only) { MLBI_DISPATCH_S(return launch_pass2<SS, true>(p, b, acc_out, s)); }
-    MLBI_DISPATCH_S(return launch_pass2<SS, false>(p, b, acc_out, s));
+    if (p.drag_only) { MLBI_DISPATCH_S(return (launch_pass2<SS, true>(p, b, acc_out, s))); }
+    MLBI_DISPATCH_S(return (launch_pass2<SS, false>(p, b, acc_out, s)));
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+{
+    if (p.drag_only) { MLBI_DISPATCH_S(return (launch_pass2_collide<SS, true>(p, b, cur, s))); }
+    MLBI_DISPATCH_S(return (launch_pass2_collide<SS, false>(p, b, cur, s)));
     return cudaErrorInvalidValue;
 }

@@ -22,6 +22,7 @@ MLB_Q = 19
 MLB_MAX_SPECIES = 4
 MLB_DRAG_ONLY = 1
 MLB_FORCE_EXPLICIT = 2
+MLB_SPLIT_COLLIDE = 4
 
 STATUS = {0: "MLB_OK", 1: "MLB_EINVAL", 2: "MLB_ENOMEM", 3: "MLB_ECUDA", 4: "MLB_ENUMERIC",
           5: "MLB_ETIMEOUT", 6: "MLB_ESTATE"}
@@ -143,10 +144,12 @@ class Simulation:
     """One mlb context for a ``workloads.Lattice``.
 
     stream: a torch.cuda.Stream (default: torch's current stream);
-    torch_alloc: take device memory from torch's caching allocator.
+    torch_alloc: take device memory from torch's caching allocator;
+    split_collide: launch pass 2 and the collision separately (MLB_SPLIT_COLLIDE)
+    instead of the fused kernel; the populations are bitwise the same.
     """
 
-    def __init__(self, lat, stream=None, torch_alloc: bool = True):
+    def __init__(self, lat, stream=None, torch_alloc: bool = True, split_collide: bool = False):
         import torch
         self.lat = lat
         self.S = lat.nspecies
@@ -159,7 +162,7 @@ class Simulation:
         d.nspecies = self.S
         d.wall_axis = lat.wall_axis
         d.flags = (MLB_DRAG_ONLY if lat.drag_only else 0) | (
-            MLB_FORCE_EXPLICIT if lat.force_scheme == "explicit" else 0)
+            MLB_FORCE_EXPLICIT if lat.force_scheme == "explicit" else 0) | (MLB_SPLIT_COLLIDE if split_collide else 0)
         for k in range(3):
             d.wall_u_lo[k] = lat.wall_u_lo[k]
             d.wall_u_hi[k] = lat.wall_u_hi[k]

@@ -179,6 +179,42 @@ def test_external_force_and_initial_velocities(gpu, orc):
     assert ok(w), w
 
 
+def _fused_case(case):
+    if case == "cube":
+        lat, n = W.binary_config1((40, 12, 10))
+    elif case == "tile2_walls":
+        lat = W.Lattice(shape=(36, 10, 12), sigma=[2.0, 1.5], wall_axis=2, wall_u_lo=(-0.02, 0.0, 0.0),
+                        wall_u_hi=(0.02, 0.0, 0.0))
+        n = W.noise(lat, W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5]), 0.03, seed=7)
+    elif case == "global_attraction":
+        lat, n = W.binary_attraction((18, 16, 17), seed=3)
+    else:
+        lat = W.Lattice(shape=(24, 9, 8), sigma=[1.0, 2.0], tau=0.8, drag_only=True)
+        n = W.noise(lat, W.densities_from_packing(0.1, lat.sigma, [0.5, 0.5]), 0.05, seed=4)
+    return lat, n
+
+
+@pytest.mark.parametrize("case", ["cube", "tile2_walls", "global_attraction", "drag"])
+def test_fused_pass2_collide_is_bitwise_split(gpu, case):
+    """The fused pass-2 + collision launch and the split pair (acceleration
+    stored, then collided) give the same populations bit for bit (the
+    global-memory passes of reach 3 always run split)."""
+    lat, n = _fused_case(case)
+    u = W.random_velocities(lat, 0.01, seed=5)
+    out = []
+    for split in (False, True):
+        sim = gpu.Simulation(lat, split_collide=split)
+        local_g = case == "cube"                 # every smoothing ball is the single site
+        untiled = case == "global_attraction"     # shell reach 3: global-memory passes, never fused
+        assert sim.launches_per_step() == (1 if local_g else 2) + (3 if split or untiled else 2) + (
+            1 if case == "global_attraction" else 0)
+        sim.set_fields(n, u)
+        sim.step(25)
+        out.append(sim.populations()[0])
+        sim.close()
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+
+
 def test_conservation_sums(gpu):
     lat, n = W.binary_attraction((20, 18, 16), seed=5)
     sim = gpu.Simulation(lat)
