@@ -402,7 +402,7 @@ mlb_status forces(mlb_ctx *c)
 // pass 2, collision and streaming of one step (after forces())
 mlb_status advance(mlb_ctx *c)
 {
-    if ((c->desc.flags & MLB_SPLIT_COLLIDE) || !c->p.tile_r) {
+    if ((c->desc.flags & MLB_SPLIT_COLLIDE) || !mlbi_pass2_collide_supported(c->p)) {
         { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
         { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream)); }
     } else {
@@ -701,7 +701,7 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;
-    const bool split = (c->desc.flags & MLB_SPLIT_COLLIDE) || !c->p.tile_r;
+    const bool split = (c->desc.flags & MLB_SPLIT_COLLIDE) || !mlbi_pass2_collide_supported(c->p);
     return (c->p.local_g ? 1 : 2) + (split ? 3 : 2) + (c->p.attr_r ? 1 : 0);
 }
 

@@ -104,7 +104,9 @@ cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, i
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s);
 cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 // pass 2 fused with the collision and streaming of f[cur] -> f[cur ^ 1] (no acceleration
-// stored); shared-memory tiled passes only (tile_r > 0), else cudaErrorInvalidValue
+// stored); only where mlbi_pass2_collide_supported (tiled passes whose fused tile fits
+// in shared memory), else cudaErrorInvalidValue
+bool mlbi_pass2_collide_supported(const mlbi_params &p);
 cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_init(const mlbi_params &p, const mlbi_buffers &b, int cur, const double *n,
                              const double *u, cudaStream_t s);

@@ -214,10 +214,10 @@ __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *s
 }
 
 // the acceleration of the site at ring position kz of the tile (centre slot cs)
+// (acc holds the rest force frest on entry)
 template <int S, int R, bool DRAG>
 __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *__restrict__ tab, const float4 *sf,
-                                           const float *sg, int kz, int cidx, const float4 *__restrict__ frest,
-                                           long long r, float (&acc)[S][3])
+                                           const float *sg, int kz, int cidx, float (&acc)[S][3])
 {
     using T = Tile<S, R>;
     const int cs = ring(kz, T::NSLOT);
@@ -231,11 +231,6 @@ __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entr
     for (int a = 0; a < S; ++a) {
         const float4 v = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
         us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
-    }
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const float4 fr = frest[a * p.N + r];
-        acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
     }
     if constexpr (R == 1) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
     else pass2_tile_shells<S, R, DRAG>(p, tab, sf, sg, kz, cidx, w, us, acc);
@@ -272,40 +267,55 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const
         if (!active) continue;
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
         float acc[S][3];
-        pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, frest, r, acc);
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const float4 fr = frest[a * p.N + r];
+            acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
+        }
+        pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, acc);
         store_acc<S>(p, r, acc, acc_f, acc_out);
     }
 }
 
 // ------------------------------------------------------------------ pass 2 fused with the collision
 // Per plane, each thread computes the acceleration of its site and at once
-// collides and streams the site.  The site's own populations and moments for
-// the next plane are prefetched by cp.async into a per-thread slot of shared
+// collides and streams the site.  Its own populations and moments for the
+// next plane are prefetched by cp.async into a per-thread slot of shared
 // memory while this plane's shell sums run.  Two cp.async groups per plane,
-// committed by every thread (empty where there is nothing to copy): A = the
-// next halo plane of the stencil ring, F = the next populations.  Waiting for
-// "all but the newest group" therefore means "the ring" at the top of the
-// plane and "the populations" before the collision.
+// committed by every thread (empty where there is nothing to copy):
+//   A(z) = halo plane z + R of the stencil ring and the site's frest(z),
+//   P(z) = the site's populations and moments of plane z.
+// They alternate A(z), P(z), A(z+1), P(z+1), ..., so "all but the newest
+// group" is A(z) at the top of plane z and P(z) before its collision.
 template <int S, int R>
 struct FusedTile {
     using T = Tile<S, R>;
     static constexpr size_t pops_off = T::bytes;                                   // float [S*19][NT]
     static constexpr size_t mom_off = pops_off + (size_t)S * MLBI_Q * T::NT * sizeof(float);   // float4 [S][NT]
-    static constexpr size_t bytes = mom_off + (size_t)S * T::NT * sizeof(float4);
+    static constexpr size_t rest_off = mom_off + (size_t)S * T::NT * sizeof(float4);           // float4 [S][NT]
+    static constexpr size_t bytes = rest_off + (size_t)S * T::NT * sizeof(float4);
 };
 
 template <int S>
-__device__ __forceinline__ void stage_site(const mlbi_params &p, long long r, int tid, int nt,
-                                           const float *__restrict__ fin, const float4 *__restrict__ mom,
-                                           float *sF, float4 *sM)
+__device__ __forceinline__ void stage_pops(const mlbi_params &p, long long r, int tid, int nt,
+                                           const float *__restrict__ fin, const float4 *__restrict__ mom, float *sF,
+                                           float4 *sM)
 {
 #pragma unroll
     for (int a = 0; a < S; ++a) {
+        cp_async16(sM + a * nt + tid, mom + a * p.N + r);
 #pragma unroll
         for (int i = 0; i < MLBI_Q; ++i)
             cp_async4(sF + (a * MLBI_Q + i) * nt + tid, fin + ((long long)a * MLBI_Q + i) * p.N + r);
-        cp_async16(sM + a * nt + tid, mom + a * p.N + r);
     }
+}
+
+template <int S>
+__device__ __forceinline__ void stage_rest(const mlbi_params &p, long long r, int tid, int nt,
+                                           const float4 *__restrict__ frest, float4 *sR)
+{
+#pragma unroll
+    for (int a = 0; a < S; ++a) cp_async16(sR + a * nt + tid, frest + a * p.N + r);
 }
 
 __device__ __forceinline__ void cp_async_wait_all_but_newest() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -327,6 +337,7 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
     float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);
     float *sF = reinterpret_cast<float *>(reinterpret_cast<char *>(smem) + F::pops_off);
     float4 *sM = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem) + F::mom_off);
+    float4 *sR = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem) + F::rest_off);
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
@@ -337,19 +348,30 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
     int xy[T::J];
     stage_sites<S, R>(p, x0, y0, xy);
     for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    if (active) stage_rest<S>(p, sxy + nxy * z0, tid, T::NT, frest, sR);
     cp_async_commit();                                                  // A(z0)
-    if (active) stage_site<S>(p, sxy + nxy * z0, tid, T::NT, fin, mom, sF, sM);
-    cp_async_commit();                                                  // F(z0)
+    if (active) stage_pops<S>(p, sxy + nxy * z0, tid, T::NT, fin, mom, sF, sM);
+    cp_async_commit();                                                  // P(z0)
     for (int z = z0; z < z1; ++z) {
         cp_async_wait_all_but_newest();                                 // A(z) landed
         __syncthreads();
         const int kz = z - z0 + R;
-        if (z + 1 < z1) stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
-        cp_async_commit();                                              // A(z + 1)
         const long long r = sxy + nxy * z;
         float acc[S][3];
-        if (active) pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, frest, r, acc);
-        cp_async_wait_all_but_newest();                                 // F(z) landed (own slots only)
+        if (active) {
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                const float4 v = sR[a * T::NT + tid];
+                acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z;
+            }
+        }
+        if (z + 1 < z1) {
+            stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
+            if (active) stage_rest<S>(p, r + nxy, tid, T::NT, frest, sR);
+        }
+        cp_async_commit();                                              // A(z + 1)
+        if (active) pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, acc);
+        cp_async_wait_all_but_newest();                                 // P(z) landed (own slots only)
         if (active) {
             Centre<S> c;
 #pragma unroll
@@ -360,9 +382,9 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
                 c.u[a][0] = v.y; c.u[a][1] = v.z; c.u[a][2] = v.w;
             }
             collide_push<S>(p, x, y, z, r, c, acc, SharedPops{sF + tid, T::NT}, fout);
-            if (z + 1 < z1) stage_site<S>(p, r + nxy, tid, T::NT, fin, mom, sF, sM);
+            if (z + 1 < z1) stage_pops<S>(p, r + nxy, tid, T::NT, fin, mom, sF, sM);
         }
-        cp_async_commit();                                              // F(z + 1)
+        cp_async_commit();                                              // P(z + 1)
     }
     cp_async_wait_all();
 }
@@ -389,10 +411,15 @@ cudaError_t launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *ac
     return cudaGetLastError();
 }
 
+constexpr size_t kMaxSharedPerBlock = 227 * 1024;
+
 template <int S, int R, bool DRAG>
 cudaError_t launch_pass2_collide_tiled(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
 {
     using F = FusedTile<S, R>;
+    if constexpr (F::bytes > kMaxSharedPerBlock) {
+        return cudaErrorInvalidValue;
+    } else {
     auto k = k_pass2_collide<S, R, DRAG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::bytes);
     if (e != cudaSuccess) return e;
@@ -400,6 +427,15 @@ cudaError_t launch_pass2_collide_tiled(const mlbi_params &p, const mlbi_buffers 
                  (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
     k<<<g, dim3(kBX, kBY), F::bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.mom, b.f[cur], b.f[cur ^ 1]);
     return cudaGetLastError();
+    }
+}
+
+template <int S>
+bool collide_fits(int tile_r)
+{
+    if (tile_r == 1) return FusedTile<S, 1>::bytes <= kMaxSharedPerBlock;
+    if (tile_r == 2) return FusedTile<S, 2>::bytes <= kMaxSharedPerBlock;
+    return false;
 }
 
 template <int S, bool DRAG>
@@ -417,6 +453,17 @@ cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, doubl
     if (p.drag_only) { MLBI_DISPATCH_S(return (launch_pass2<SS, true>(p, b, acc_out, s))); }
     MLBI_DISPATCH_S(return (launch_pass2<SS, false>(p, b, acc_out, s)));
     return cudaErrorInvalidValue;
+}
+
+bool mlbi_pass2_collide_supported(const mlbi_params &p)
+{
+    switch (p.S) {
+    case 1: return collide_fits<1>(p.tile_r);
+    case 2: return collide_fits<2>(p.tile_r);
+    case 3: return collide_fits<3>(p.tile_r);
+    case 4: return collide_fits<4>(p.tile_r);
+    default: return false;
+    }
 }
 
 cudaError_t mlbi_launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
