@@ -1,12 +1,52 @@
-// mlb_collide.cuh -- the collision and push streaming of one site, shared by
-// the stand-alone collision kernel (mlb_kernels.cu) and the fused pass-2 +
-// collision kernels (mlb_pass2.cu).  Internal header.
+// mlb_collide.cuh -- the moments, collision and push streaming of one site,
+// shared by the stand-alone kernels (mlb_kernels.cu) and the fused pass-2 +
+// collision kernels (mlb_pass2.cu), which must agree bit for bit.  Internal
+// header.
 #pragma once
 
 #include "mlb_internal.h"
 #include "mlb_device.cuh"
 
 namespace {
+
+// ------------------------------------------------------------------ moments
+// dn = sum_i f_i (f stored minus w_i n_ref), j = sum_i c_i f_i taken as the
+// differences of opposite links first, u = j / n (the barycentric velocity
+// where n is tiny), for every species.
+template <int S, class Pops>
+__device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &pops, float (&dn)[S], float (&u)[S][3])
+{
+    float jx[S], jy[S], jz[S], rho = 0.f, m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        float v[MLBI_Q];
+#pragma unroll
+        for (int i = 0; i < MLBI_Q; ++i) v[i] = pops(a, i);
+        float m0 = v[0], mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int i = 1; i < MLBI_Q; i += 2) {
+            m0 += v[i] + v[i + 1];
+            const float d = v[i] - v[i + 1];          // opposite links i, i + 1
+            if (CX[i]) mx += CX[i] * d;
+            if (CY[i]) my += CY[i] * d;
+            if (CZ[i]) mz += CZ[i] * d;
+        }
+        dn[a] = m0;
+        jx[a] = mx; jy[a] = my; jz[a] = mz;
+        rho += p.nref[a] + m0;
+        m[0] += mx; m[1] += my; m[2] += mz;
+    }
+    const float irho = rho > 0.f ? 1.f / rho : 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        const float n = p.nref[a] + dn[a];
+        const bool ok = n > kTinyDensity;
+        const float in = ok ? 1.f / n : 0.f;
+        u[a][0] = ok ? jx[a] * in : m[0] * irho;
+        u[a][1] = ok ? jy[a] * in : m[1] * irho;
+        u[a][2] = ok ? jz[a] * in : m[2] * irho;
+    }
+}
 
 // ------------------------------------------------------------------ collide + stream
 // Collision toward psi_perp at u + a/2 (Eq. prefactor, Hermite-2) with the

@@ -29,48 +29,6 @@
 #include <math.h>
 
 namespace {
-// ------------------------------------------------------------------ moments
-// dn = sum_i f_i (f stored minus w_i n_ref), j = sum_i c_i f_i taken as the
-// differences of opposite links first, u = j / n (the barycentric velocity
-// where n is tiny).  Writes (dn, u) of every species.
-template <int S>
-__device__ __forceinline__ void site_moments(const mlbi_params &p, const float *__restrict__ f, long long r,
-                                             float (&dn)[S], float (&u)[S][3])
-{
-    const long long N = p.N;
-    float jx[S], jy[S], jz[S], rho = 0.f, m[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const float *fa = f + (long long)a * MLBI_Q * N + r;
-        float v[MLBI_Q];
-#pragma unroll
-        for (int i = 0; i < MLBI_Q; ++i) v[i] = __ldg(fa + i * N);
-        float m0 = v[0], mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-        for (int i = 1; i < MLBI_Q; i += 2) {
-            m0 += v[i] + v[i + 1];
-            const float d = v[i] - v[i + 1];          // opposite links i, i + 1
-            if (CX[i]) mx += CX[i] * d;
-            if (CY[i]) my += CY[i] * d;
-            if (CZ[i]) mz += CZ[i] * d;
-        }
-        dn[a] = m0;
-        jx[a] = mx; jy[a] = my; jz[a] = mz;
-        rho += p.nref[a] + m0;
-        m[0] += mx; m[1] += my; m[2] += mz;
-    }
-    const float irho = rho > 0.f ? 1.f / rho : 0.f;
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const float n = p.nref[a] + dn[a];
-        const bool ok = n > kTinyDensity;
-        const float in = ok ? 1.f / n : 0.f;
-        u[a][0] = ok ? jx[a] * in : m[0] * irho;
-        u[a][1] = ok ? jy[a] * in : m[1] * irho;
-        u[a][2] = ok ? jz[a] * in : m[2] * irho;
-    }
-}
-
 template <int S>
 __global__ void __launch_bounds__(kBlock) k_moments(const mlbi_params p, const float *__restrict__ f,
                                                     float4 *__restrict__ mom)
@@ -79,7 +37,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const mlbi_params p, const f
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
         float dn[S], u[S][3];
-        site_moments<S>(p, f, r, dn, u);
+        site_moments<S>(p, GlobalPops{f + r, N}, dn, u);
 #pragma unroll
         for (int a = 0; a < S; ++a) mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
     }
@@ -141,7 +99,7 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
         float dn[S], u[S][3];
-        site_moments<S>(p, f, r, dn, u);
+        site_moments<S>(p, GlobalPops{f + r, N}, dn, u);
         float d2 = 0.f, d3 = 0.f;
 #pragma unroll
         for (int a = 0; a < S; ++a) {
