@@ -36,7 +36,7 @@ UNIT = "MLUPS/species"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mlb", "reference"], default="mlb")
     ap.add_argument("--size", type=int, default=None, help="cubic lattice extent (default: the workload's)")
