@@ -296,7 +296,7 @@ __device__ __forceinline__ void pass1_cube(const mlbi_params &p, const float4 *s
 }
 
 template <int S, int R, bool DRAG>
-__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom,
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 6 : 2) k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom,
                                                               const float *__restrict__ dg,
                                                               const mlbi_entry *__restrict__ tab,
                                                               const float4 *__restrict__ fext,
