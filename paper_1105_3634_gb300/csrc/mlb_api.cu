@@ -110,7 +110,7 @@ mlb_status rebuild(mlb_ctx *c)
             const double sab = 0.5 * (c->sigma[a] + c->sigma[b]);
             shell_reach = std::max(shell_reach, (int)std::floor(std::sqrt(std::pow(sab + 0.5, 2) - 1e-9)));
         }
-    const int tile_r = shell_reach <= 2 ? shell_reach : 0;
+    const int tile_r = mlbi_tile_ty(S, shell_reach) ? shell_reach : 0;
     const int txh = 32 + 2 * tile_r;
     // reach of the attraction regions (column attraction kernel if <= 8)
     int attr_reach = 0;

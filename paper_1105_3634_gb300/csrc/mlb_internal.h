@@ -60,7 +60,7 @@ struct mlbi_params {
     int ushell_start[MLBI_MAXS], ushell_count[MLBI_MAXS];   // union half shells per neighbour species
     int reach;                       // largest offset component of any stencil (>= 1)
     int local_g;                     // every smoothing ball is the single site
-    int tile_r;                      // reach of the union shells if the tiled kernels serve it (1, 2), else 0
+    int tile_r;                      // reach of the union shells if the tiled kernels serve it (1..3), else 0
     int cube_mask[MLBI_MAXP];        // tile_r == 1: bit k set when half offset k of the 3x3x3 cube is in S_ab
     int attr_r;                      // reach of the attraction if the column attraction kernel serves it (1..8), else 0
     // column form of the attraction (attr_r > 0): acol_count columns (dx, dy) of the
@@ -73,6 +73,24 @@ struct mlbi_params {
     mlbi_pair pair[MLBI_MAXP];
     float wall_lo[3], wall_hi[3];
 };
+
+// Shared-memory z-marching tiles of the stencil passes: a ring of 2R + 2
+// planes of (32 + 2R) x (ty + 2R) sites, each site S float4 fields and
+// S(S+1)/2 contact-value deviations.  Tiles serve shell reach R <= 3; reach 1
+// and 2 use 32 x 4 blocks, reach 3 32 x 8 blocks where they fit, else 32 x 4.
+#define MLBI_MAX_TILE_BYTES (227 * 1024)
+__host__ __device__ constexpr long long mlbi_tile_bytes(int S, int R, int ty)
+{
+    return (long long)(2 * R + 2) * (32 + 2 * R) * (ty + 2 * R) * (S * 16 + S * (S + 1) / 2 * 4);
+}
+// block height of the tile for (S, R), or 0 when no tile fits (global-memory passes)
+__host__ __device__ constexpr int mlbi_tile_ty(int S, int R)
+{
+    return R < 1 || R > 3 ? 0
+         : R < 3 ? (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES ? 4 : 0)
+         : mlbi_tile_bytes(S, R, 8) <= MLBI_MAX_TILE_BYTES ? 8
+         : (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES ? 4 : 0);
+}
 
 // Device buffers of one context (all carved from one allocation).
 struct mlbi_buffers {

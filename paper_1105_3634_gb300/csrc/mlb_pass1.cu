@@ -3,7 +3,7 @@
 // the friction matrix Gamma^a, the attraction read-in, and the half-step
 // predictor du of the semi-implicit forcing.  Three variants of the shell
 // sums: global-memory (any reach), shared-memory tile with the stencil table
-// (reach 2), and the compile-time 3x3x3 cube (reach 1).
+// (reach 2, 3), and the compile-time 3x3x3 cube (reach 1).
 #include "mlb_passes.cuh"
 
 namespace {
@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass1(const mlbi_params p, const 
 
 // ------------------------------------------------------------------ tiled variants
 // Shell sums from the tile with the stencil table (same sums as pass1_shells).
-template <int S, int R, bool DRAG>
+template <int S, int R, bool DRAG, int TY>
 __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
                                                   const float4 *sf, const float *sg, int kz, int cidx,
                                                   const Centre<S> &c, const PairW<S> &w, Acc1<S> &A)
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
 #pragma unroll
     for (int b = 0; b < S; ++b) {
         const float nr = p.nref[b];
@@ -295,33 +295,32 @@ __device__ __forceinline__ void pass1_cube(const mlbi_params &p, const float4 *s
     }
 }
 
-template <int S, int R, bool DRAG>
-__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 6 : 2) k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom,
-                                                              const float *__restrict__ dg,
-                                                              const mlbi_entry *__restrict__ tab,
-                                                              const float4 *__restrict__ fext,
-                                                              const float4 *__restrict__ attr,
-                                                              float4 *__restrict__ frest, float4 *__restrict__ pst)
+template <int S, int R, bool DRAG, int TY>
+__global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S <= 2 ? 6 : 2))
+    k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom, const float *__restrict__ dg,
+                  const mlbi_entry *__restrict__ tab, const float4 *__restrict__ fext, const float4 *__restrict__ attr,
+                  float4 *__restrict__ frest, float4 *__restrict__ pst)
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
     extern __shared__ float4 smem[];
     float4 *sf = smem;                                                      // [NSLOT][S][PLANE]
     float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);   // [NSLOT][NP][PLANE]
-    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * TY, z0 = blockIdx.z * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active = x < p.nx && y < p.ny;
     const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
     int xy[T::J];
-    stage_sites<S, R>(p, x0, y0, xy);
-    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), mom, dg, sf, sg);
+    stage_sites<S, R, TY>(p, x0, y0, xy);
+    for (int k = 0; k < 2 * R + 1; ++k)
+        stage_plane<S, R, TY>(p, xy, z0 - R + k, ring(k, T::NSLOT), mom, dg, sf, sg);
     cp_async_commit();
     for (int z = z0; z < z1; ++z) {
         cp_async_wait_all();
         __syncthreads();
         const int kz = z - z0 + R;                      // ring position of plane z
         if (z + 1 < z1) {
-            stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), mom, dg, sf, sg);
+            stage_plane<S, R, TY>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), mom, dg, sf, sg);
             cp_async_commit();
         }
         if (!active) continue;
@@ -343,8 +342,8 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 6 : 2) k_pass1_tiled(const
         pair_weights<S>(p, dgc, w);
         Acc1<S> A;
         A.zero();
-        if constexpr (R == 1) pass1_cube<S, DRAG>(p, sf, sg, kz, cidx, c, w, A);
-        else pass1_tile_shells<S, R, DRAG>(p, tab, sf, sg, kz, cidx, c, w, A);
+        if constexpr (R == 1 && TY == kBY) pass1_cube<S, DRAG>(p, sf, sg, kz, cidx, c, w, A);
+        else pass1_tile_shells<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, c, w, A);
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
         if (p.attr_r) {
 #pragma unroll
@@ -367,14 +366,19 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 6 : 2) k_pass1_tiled(const
 template <int S, int R, bool DRAG>
 cudaError_t launch_pass1_tiled(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
 {
-    using T = Tile<S, R>;
-    auto k = k_pass1_tiled<S, R, DRAG>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
-    if (e != cudaSuccess) return e;
-    const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
-                 (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
-    k<<<g, dim3(kBX, kBY), T::bytes, s>>>(p, b.mom, b.dg, b.table, b.fext, b.attr, b.frest, b.pst);
-    return cudaGetLastError();
+    constexpr int TY = mlbi_tile_ty(S, R);
+    if constexpr (TY == 0) {
+        return cudaErrorInvalidValue;
+    } else {
+        using T = Tile<S, R, TY>;
+        auto k = k_pass1_tiled<S, R, DRAG, TY>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+        if (e != cudaSuccess) return e;
+        const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + TY - 1) / TY),
+                     (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+        k<<<g, dim3(kBX, TY), T::bytes, s>>>(p, b.mom, b.dg, b.table, b.fext, b.attr, b.frest, b.pst);
+        return cudaGetLastError();
+    }
 }
 
 template <int S, bool DRAG>
@@ -382,6 +386,7 @@ cudaError_t launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream
 {
     if (p.tile_r == 1) return launch_pass1_tiled<S, 1, DRAG>(p, b, s);
     if (p.tile_r == 2) return launch_pass1_tiled<S, 2, DRAG>(p, b, s);
+    if (p.tile_r == 3) return launch_pass1_tiled<S, 3, DRAG>(p, b, s);
     k_pass1<S, DRAG><<<tiled_grid(p), dim3(kBX, kBY), 0, s>>>(p, b.mom, b.dg, b.table, b.fext, b.attr, b.frest,
                                                                 b.pst);
     return cudaGetLastError();

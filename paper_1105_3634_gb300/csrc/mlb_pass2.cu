@@ -2,7 +2,7 @@
 // (Eqs. gammaab, viscousforce) at the predicted velocities u* of pass 1,
 // completed to the acceleration a^a = frest^a + sum_points s sd (masses 1).
 // Same three variants as pass 1: global memory, tile with the stencil table
-// (reach 2), compile-time 3x3x3 cube (reach 1).  The tiled variants also come
+// (reach 2, 3), compile-time 3x3x3 cube (reach 1).  The tiled variants also come
 // fused with the collision (k_pass2_collide): the acceleration is not stored,
 // the same thread collides and streams its site right away (the collision
 // needs only the site's own acceleration).
@@ -113,12 +113,12 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const 
 }
 
 // ------------------------------------------------------------------ tiled variants
-template <int S, int R, bool DRAG>
+template <int S, int R, bool DRAG, int TY>
 __device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
                                                   const float4 *sf, const float *sg, int kz, int cidx,
                                                   const PairW<S> &w, const float (&us)[S][3], float (&acc)[S][3])
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
 #pragma unroll
     for (int b = 0; b < S; ++b) {
         const float nr = p.nref[b];
@@ -215,11 +215,11 @@ __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *s
 
 // the acceleration of the site at ring position kz of the tile (centre slot cs)
 // (acc holds the rest force frest on entry)
-template <int S, int R, bool DRAG>
+template <int S, int R, bool DRAG, int TY>
 __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *__restrict__ tab, const float4 *sf,
                                            const float *sg, int kz, int cidx, float (&acc)[S][3])
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
     const int cs = ring(kz, T::NSLOT);
     float dgc[T::NP];
 #pragma unroll
@@ -232,36 +232,36 @@ __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entr
         const float4 v = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
         us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
     }
-    if constexpr (R == 1) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
-    else pass2_tile_shells<S, R, DRAG>(p, tab, sf, sg, kz, cidx, w, us, acc);
+    if constexpr (R == 1 && TY == kBY) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
+    else pass2_tile_shells<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, w, us, acc);
 }
 
-template <int S, int R, bool DRAG>
-__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const mlbi_params p, const float *__restrict__ dg,
-                                                              const mlbi_entry *__restrict__ tab,
-                                                              const float4 *__restrict__ frest,
-                                                              const float4 *__restrict__ pst,
-                                                              float4 *__restrict__ acc_f, double *__restrict__ acc_out)
+template <int S, int R, bool DRAG, int TY>
+__global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S <= 2 ? 4 : 2))
+    k_pass2_tiled(const mlbi_params p, const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
+                  const float4 *__restrict__ frest, const float4 *__restrict__ pst, float4 *__restrict__ acc_f,
+                  double *__restrict__ acc_out)
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
     extern __shared__ float4 smem[];
     float4 *sf = smem;
     float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);
-    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * TY, z0 = blockIdx.z * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active = x < p.nx && y < p.ny;
     const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
     int xy[T::J];
-    stage_sites<S, R>(p, x0, y0, xy);
-    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    stage_sites<S, R, TY>(p, x0, y0, xy);
+    for (int k = 0; k < 2 * R + 1; ++k)
+        stage_plane<S, R, TY>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
     cp_async_commit();
     for (int z = z0; z < z1; ++z) {
         cp_async_wait_all();
         __syncthreads();
         const int kz = z - z0 + R;
         if (z + 1 < z1) {
-            stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
+            stage_plane<S, R, TY>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
             cp_async_commit();
         }
         if (!active) continue;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2) k_pass2_tiled(const
             const float4 fr = frest[a * p.N + r];
             acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
         }
-        pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, acc);
+        pass2_site<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, acc);
         store_acc<S>(p, r, acc, acc_f, acc_out);
     }
 }
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
             if (active) stage_rest<S>(p, r + nxy, tid, T::NT, frest, sR);
         }
         cp_async_commit();                                              // A(z + 1)
-        if (active) pass2_site<S, R, DRAG>(p, tab, sf, sg, kz, cidx, acc);
+        if (active) pass2_site<S, R, DRAG, kBY>(p, tab, sf, sg, kz, cidx, acc);
         cp_async_wait_all_but_newest();                                 // P(z) landed (own slots only)
         if (active) {
             Centre<S> c;
@@ -392,14 +392,19 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
 template <int S, int R, bool DRAG>
 cudaError_t launch_pass2_tiled(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
 {
-    using T = Tile<S, R>;
-    auto k = k_pass2_tiled<S, R, DRAG>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
-    if (e != cudaSuccess) return e;
-    const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
-                 (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
-    k<<<g, dim3(kBX, kBY), T::bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
-    return cudaGetLastError();
+    constexpr int TY = mlbi_tile_ty(S, R);
+    if constexpr (TY == 0) {
+        return cudaErrorInvalidValue;
+    } else {
+        using T = Tile<S, R, TY>;
+        auto k = k_pass2_tiled<S, R, DRAG, TY>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+        if (e != cudaSuccess) return e;
+        const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + TY - 1) / TY),
+                     (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+        k<<<g, dim3(kBX, TY), T::bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
+        return cudaGetLastError();
+    }
 }
 
 template <int S, bool DRAG>
@@ -407,6 +412,7 @@ cudaError_t launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *ac
 {
     if (p.tile_r == 1) return launch_pass2_tiled<S, 1, DRAG>(p, b, acc_out, s);
     if (p.tile_r == 2) return launch_pass2_tiled<S, 2, DRAG>(p, b, acc_out, s);
+    if (p.tile_r == 3) return launch_pass2_tiled<S, 3, DRAG>(p, b, acc_out, s);
     k_pass2<S, DRAG><<<tiled_grid(p), dim3(kBX, kBY), 0, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
     return cudaGetLastError();
 }

@@ -102,30 +102,38 @@ __device__ __forceinline__ Nb fetch_nb(const mlbi_params &p, const Loc &L, const
 }
 
 // ------------------------------------------------------------------ shared-memory tiles (z marching)
-// A block of 32 x 4 threads owns a 32 x 4 column of sites and marches up z
+// A block of 32 x TY threads owns a 32 x TY column of sites and marches up z
 // through `zchunk` planes.  The stencil field of every species (float4: the
 // moments in pass 1, (n - n_ref, u*) in pass 2) and the contact-value
 // deviations of every pair are staged in shared memory as a ring of planes
-// of (32 + 2R) x (4 + 2R) sites: 2R + 1 planes in use and one more being
+// of (32 + 2R) x (TY + 2R) sites: 2R + 1 planes in use and one more being
 // filled by cp.async while the current plane is computed.  Every shell
 // neighbour is then read from shared memory.
-template <int S, int R>
+template <int S, int R, int TY_ = kBY>
 struct Tile {
-    static constexpr int TX = kBX, TY = kBY;
+    static constexpr int TX = kBX, TY = TY_;
     static constexpr int TXH = TX + 2 * R, TYH = TY + 2 * R, PLANE = TXH * TYH;
     static constexpr int NSLOT = 2 * R + 2;
     static constexpr int NP = S * (S + 1) / 2;
-    static constexpr int NT = kBX * kBY;
+    static constexpr int NT = kBX * TY;
     static constexpr int J = (PLANE + NT - 1) / NT;          // staging sites per thread and plane
     static constexpr size_t bytes = (size_t)NSLOT * PLANE * (S * sizeof(float4) + NP * sizeof(float));
+    static_assert(bytes == (size_t)mlbi_tile_bytes(S, R, TY), "tile size formula");
 };
+
+// resident blocks per SM the tile's shared memory allows (at most `cap`)
+constexpr int tile_blocks(size_t bytes, int cap)
+{
+    const int b = (int)((228 * 1024) / (bytes + 1024));
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
 
 // (x, y) offsets x + nx y of this thread's staging sites, fixed while the
 // block marches up z; -1 beyond a wall
-template <int S, int R>
-__device__ __forceinline__ void stage_sites(const mlbi_params &p, int x0, int y0, int (&xy)[Tile<S, R>::J])
+template <int S, int R, int TY = kBY>
+__device__ __forceinline__ void stage_sites(const mlbi_params &p, int x0, int y0, int (&xy)[Tile<S, R, TY>::J])
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
     const int tid = threadIdx.y * kBX + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < T::J; ++j) {
@@ -147,12 +155,12 @@ __device__ __forceinline__ int wrap_plane(int c, int L, bool wall)
 // Stage plane gz of the tile into ring slot `slot`.  Sites beyond a wall get
 // n = 0 (n - n_ref = -n_ref) and zero velocity; their dg is never used (every
 // term carries n(r+d) = 0) and is set to 0.
-template <int S, int R>
-__device__ __forceinline__ void stage_plane(const mlbi_params &p, const int (&xy)[Tile<S, R>::J], int gz, int slot,
-                                            const float4 *__restrict__ fld, const float *__restrict__ dg,
+template <int S, int R, int TY = kBY>
+__device__ __forceinline__ void stage_plane(const mlbi_params &p, const int (&xy)[Tile<S, R, TY>::J], int gz,
+                                            int slot, const float4 *__restrict__ fld, const float *__restrict__ dg,
                                             float4 *sf, float *sg)
 {
-    using T = Tile<S, R>;
+    using T = Tile<S, R, TY>;
     const long long N = p.N;
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const int z = wrap_plane(gz, p.nz, p.wall_axis == 2);

@@ -156,6 +156,17 @@ def test_taylor_channel_three_species_walls(gpu, orc):
     assert ok(w), w
 
 
+def test_global_memory_passes_reach4(gpu, orc):
+    """sigma = (4, 3): contact shells of reach 4, beyond the shared-memory
+    tiles, so both passes read neighbours from global memory; 40 steps."""
+    lat = W.Lattice(shape=(20, 16, 14), sigma=[4.0, 3.0], tau=0.9)
+    n0 = W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5])
+    n = W.noise(lat, n0, 0.02, seed=41)
+    u = W.random_velocities(lat, 0.005, seed=42)
+    w = run_pair(gpu, orc, lat, n, u, checkpoints=(0, 1, 40))
+    assert ok(w), w
+
+
 @pytest.mark.parametrize("drag_only,scheme", [(True, "semi_implicit"), (False, "explicit"), (True, "explicit")])
 def test_flags_drag_only_and_forward_euler(gpu, orc, drag_only, scheme):
     lat = W.Lattice(shape=(24, 9, 8), sigma=[1.0, 2.0], tau=0.8, drag_only=drag_only, force_scheme=scheme)
@@ -197,15 +208,15 @@ def _fused_case(case):
 @pytest.mark.parametrize("case", ["cube", "tile2_walls", "global_attraction", "drag"])
 def test_fused_pass2_collide_is_bitwise_split(gpu, case):
     """The fused pass-2 + collision launch and the split pair (acceleration
-    stored, then collided) give the same populations bit for bit (the
-    global-memory passes of reach 3 always run split)."""
+    stored, then collided) give the same populations bit for bit (shells of
+    reach 3 always run split)."""
     lat, n = _fused_case(case)
     u = W.random_velocities(lat, 0.01, seed=5)
     out = []
     for split in (False, True):
         sim = gpu.Simulation(lat, split_collide=split)
         local_g = case == "cube"                 # every smoothing ball is the single site
-        untiled = case == "global_attraction"     # shell reach 3: global-memory passes, never fused
+        untiled = case == "global_attraction"     # shell reach 3: never fused
         assert sim.launches_per_step() == (1 if local_g else 2) + (3 if split or untiled else 2) + (
             1 if case == "global_attraction" else 0)
         sim.set_fields(n, u)
