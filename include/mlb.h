@@ -160,6 +160,44 @@ mlb_status mlb_profile_enable(mlb_ctx *ctx, int32_t enable);
 int32_t mlb_profile_read(mlb_ctx *ctx, double *ms, int64_t *launches, int32_t max_kernels);
 const char *mlb_kernel_name(int32_t k);
 
+/* Work decomposition tuner (no counterpart in the paper; the physics is
+ * unchanged: every site's arithmetic is the same under every candidate, so
+ * results are bitwise identical whatever it picks).  Times `trials` force +
+ * collision passes from the current state for each candidate number of z
+ * planes per block of the stencil kernels (4, 8, 16, 32, not above nz) and,
+ * where both exist, the fused and the split pass-2 + collision launches, and
+ * keeps the fastest.  The state is untouched: a trial reads f[cur] and writes
+ * the other population buffer, and cur is not advanced.  Synchronises the
+ * context's stream.  zchunk_out / fused_out (may be NULL) receive the choice.
+ * Errors: MLB_EINVAL for trials < 1, MLB_ESTATE before fields are set. */
+mlb_status mlb_autotune(mlb_ctx *ctx, int32_t trials, int32_t *zchunk_out, int32_t *fused_out);
+
+/* Batched ensemble (no counterpart in the paper): independent contexts of any
+ * sizes and settings stepped together.  One step of every member is captured
+ * into a CUDA graph (each member's launches on its own stream, forked from
+ * and joined back to the batch stream, so the members' kernels run
+ * concurrently) and replayed; two steps are captured per graph so that the
+ * ping-pong population buffers return to their parity.  The graph is rebuilt
+ * when a member's settings or buffer parity changed since the capture.
+ *   members  n >= 1 distinct contexts on the current device, each with its own
+ *            stream (the default NULL stream of mlb_lattice_desc gives one);
+ *            the batch does not own them and they must outlive it.
+ *   stream   cudaStream_t the batch launches on; NULL = a stream it creates.
+ * mlb_batch_step(nsteps) advances every member by nsteps (an odd last step
+ * runs through mlb_step on the members' streams); work already queued on a
+ * member's stream runs first, and later work on it runs after.  It returns
+ * without waiting; mlb_batch_synchronize waits for the batch and checks every
+ * member's numeric flags.  Errors: MLB_EINVAL for bad arguments, MLB_ESTATE if
+ * a member has no fields or failed; a capture or launch error puts the batch
+ * in a failed state (every call returns MLB_ESTATE); mlb_batch_last_error
+ * gives the message. */
+typedef struct mlb_batch mlb_batch;
+mlb_status mlb_batch_create(mlb_ctx *const *members, int32_t n, void *stream, mlb_batch **out);
+mlb_status mlb_batch_step(mlb_batch *batch, int64_t nsteps);
+mlb_status mlb_batch_synchronize(mlb_batch *batch);
+const char *mlb_batch_last_error(const mlb_batch *batch);
+void mlb_batch_destroy(mlb_batch *batch);
+
 /* Conservation sums without any allocation (the paper has no counterpart:
  * this serves callers that cannot let the library allocate).  A caller whose
  * device memory is all owned by its own memory manager (a framework pool, a

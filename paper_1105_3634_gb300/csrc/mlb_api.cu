@@ -47,6 +47,11 @@ struct mlb_ctx {
     size_t ev_used = 0;
     double prof_ms[8] = {0};
     int64_t prof_count[8] = {0};
+    // work decomposition chosen by mlb_autotune (0 / -1: the defaults)
+    int tuned_zchunk = 0;
+    int tuned_split = -1;
+    // bumped whenever the kernels' parameters change (captured graphs go stale)
+    uint64_t version = 0;
 };
 
 namespace {
@@ -298,7 +303,7 @@ mlb_status rebuild(mlb_ctx *c)
         if (p.ball_count[g] != 1) p.local_g = 0;
     p.tile_r = tile_r;
     p.attr_r = attraction ? attr_r : 0;
-    p.zchunk = std::min(c->desc.nz, 16);
+    p.zchunk = std::min(c->desc.nz, c->tuned_zchunk > 0 ? c->tuned_zchunk : 16);
     // the 13 canonical half offsets of the 3x3x3 cube, in the order the kernels use:
     // (1,0,0); (-1,1,0), (0,1,0), (1,1,0); then dz = 1 with dy = -1, 0, 1 and dx = -1, 0, 1
     {
@@ -329,6 +334,7 @@ mlb_status rebuild(mlb_ctx *c)
     MLB_CUDA(c, cudaMemcpyAsync((void *)c->b.table, tab.data(), tab.size() * sizeof(mlbi_entry),
                                 cudaMemcpyHostToDevice, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    ++c->version;
     return MLB_OK;
 }
 
@@ -399,10 +405,16 @@ mlb_status forces(mlb_ctx *c)
     return MLB_OK;
 }
 
+// pass 2 and the collision as two launches (else one fused launch)
+bool split_collide(const mlb_ctx *c)
+{
+    return (c->desc.flags & MLB_SPLIT_COLLIDE) || !mlbi_pass2_collide_supported(c->p) || c->tuned_split == 1;
+}
+
 // pass 2, collision and streaming of one step (after forces())
 mlb_status advance(mlb_ctx *c)
 {
-    if ((c->desc.flags & MLB_SPLIT_COLLIDE) || !mlbi_pass2_collide_supported(c->p)) {
+    if (split_collide(c)) {
         { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
         { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream)); }
     } else {
@@ -670,6 +682,7 @@ mlb_status mlb_set_external_force(mlb_ctx *c, const double *fext)
     const long long N = c->p.N;
     if (!fext) {
         c->p.has_fext = 0;
+        ++c->version;
         return MLB_OK;
     }
     for (long long k = 0; k < (long long)S * 3 * N; ++k)
@@ -678,6 +691,7 @@ mlb_status mlb_set_external_force(mlb_ctx *c, const double *fext)
     MLB_CUDA(c, mlbi_launch_import_fext(c->p, c->b, c->b.stage, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->p.has_fext = 1;
+    ++c->version;
     return MLB_OK;
 }
 
@@ -701,8 +715,7 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;
-    const bool split = (c->desc.flags & MLB_SPLIT_COLLIDE) || !mlbi_pass2_collide_supported(c->p);
-    return (c->p.local_g ? 1 : 2) + (split ? 3 : 2) + (c->p.attr_r ? 1 : 0);
+    return (c->p.local_g ? 1 : 2) + (split_collide(c) ? 3 : 2) + (c->p.attr_r ? 1 : 0);
 }
 
 const char *mlb_kernel_name(int32_t k)
@@ -847,6 +860,66 @@ const char *mlb_last_error(const mlb_ctx *c)
     return c->err.c_str();
 }
 
+mlb_status mlb_autotune(mlb_ctx *c, int32_t trials, int32_t *zchunk_out, int32_t *fused_out)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    if (trials < 1) return fail(c, MLB_EINVAL, "trials must be >= 1");
+    const bool prof = c->profiling;
+    c->profiling = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MLB_CUDA(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, MLB_ECUDA, "cudaEventCreate failed");
+    }
+    std::vector<int> zs;
+    for (int z : {4, 8, 16, 32})
+        if (z <= c->desc.nz) zs.push_back(z);
+    if (zs.empty()) zs.push_back(c->desc.nz);
+    const bool can_fuse = !(c->desc.flags & MLB_SPLIT_COLLIDE) && mlbi_pass2_collide_supported(c->p);
+    float best = -1.f;
+    int best_z = c->p.zchunk, best_split = c->tuned_split;
+    for (int split = can_fuse ? 0 : 1; split <= 1 && st == MLB_OK; ++split) {
+        c->tuned_split = can_fuse ? split : -1;
+        for (int z : zs) {
+            c->p.zchunk = z;
+            // one untimed pass, then `trials` timed ones; cur is not advanced,
+            // so every pass reads the same f[cur] and the state is untouched
+            for (int t = 0; t <= trials && st == MLB_OK; ++t) {
+                if (t == 1) cudaEventRecord(e0, c->stream);
+                st = forces(c);
+                if (st == MLB_OK) st = advance(c);
+            }
+            if (st != MLB_OK) break;
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fail(c, MLB_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_z = z;
+                best_split = c->tuned_split;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->profiling = prof;
+    c->tuned_zchunk = best_z;
+    c->p.zchunk = best_z;
+    c->tuned_split = best_split;
+    ++c->version;
+    if (st != MLB_OK) return st;
+    if (zchunk_out) *zchunk_out = best_z;
+    if (fused_out) *fused_out = split_collide(c) ? 0 : 1;
+    return check_flags(c);
+}
+
 void mlb_destroy(mlb_ctx *c)
 {
     if (!c) return;
@@ -858,6 +931,197 @@ void mlb_destroy(mlb_ctx *c)
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched ensemble
+struct mlb_batch {
+    std::vector<mlb_ctx *> m;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> version;            // members' settings at the capture
+    std::vector<int> cur;                     // members' buffer parity at the capture
+    cudaEvent_t cap_fork = nullptr, join = nullptr;
+    std::vector<cudaEvent_t> cap_done, pre;   // per member: capture join, order before a launch
+    bool failed = false;
+    std::string err;
+};
+
+namespace {
+
+mlb_status batch_fail(mlb_batch *b, mlb_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->err = buf;
+    if (s == MLB_ECUDA) b->failed = true;
+    return s;
+}
+
+// Capture two steps of every member into a graph: fork from the batch stream
+// onto each member's stream, two (forces, advance) pairs per member, join back.
+mlb_status batch_capture(mlb_batch *b)
+{
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    mlb_status st = MLB_OK;
+    e = cudaEventRecord(b->cap_fork, b->stream);
+    for (size_t i = 0; i < b->m.size() && e == cudaSuccess && st == MLB_OK; ++i) {
+        mlb_ctx *c = b->m[i];
+        const bool prof = c->profiling;
+        c->profiling = false;
+        e = cudaStreamWaitEvent(c->stream, b->cap_fork, 0);
+        for (int k = 0; k < 2 && e == cudaSuccess && st == MLB_OK; ++k) {
+            st = forces(c);
+            if (st == MLB_OK) st = advance(c);
+            c->cur ^= 1;                      // two flips: back to the captured parity
+        }
+        c->profiling = prof;
+        if (e == cudaSuccess) e = cudaEventRecord(b->cap_done[i], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->cap_done[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = ee;
+    if (st != MLB_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st != MLB_OK) return batch_fail(b, MLB_ECUDA, "capture: member launch failed");
+        return batch_fail(b, MLB_ECUDA, "capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return batch_fail(b, MLB_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        b->version[i] = b->m[i]->version;
+        b->cur[i] = b->m[i]->cur;
+    }
+    return MLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mlb_status mlb_batch_create(mlb_ctx *const *members, int32_t n, void *stream, mlb_batch **out)
+{
+    if (!out) return MLB_EINVAL;
+    *out = nullptr;
+    if (!members || n < 1) return MLB_EINVAL;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!members[i] || members[i]->failed || !members[i]->stream) return MLB_EINVAL;
+        for (int32_t j = 0; j < i; ++j)
+            if (members[j] == members[i]) return MLB_EINVAL;
+    }
+    mlb_batch *b = new (std::nothrow) mlb_batch();
+    if (!b) return MLB_ENOMEM;
+    b->m.assign(members, members + n);
+    b->version.assign(n, 0);
+    b->cur.assign(n, -1);
+    b->cap_done.assign(n, nullptr);
+    b->pre.assign(n, nullptr);
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    const unsigned fl = cudaEventDisableTiming;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cap_fork, fl);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, fl);
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&b->cap_done[i], fl);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->pre[i], fl);
+    }
+    if (e != cudaSuccess) {
+        mlb_batch_destroy(b);
+        return MLB_ECUDA;
+    }
+    *out = b;
+    return MLB_OK;
+}
+
+mlb_status mlb_batch_step(mlb_batch *b, int64_t nsteps)
+{
+    if (!b) return MLB_EINVAL;
+    if (b->failed) return MLB_ESTATE;
+    if (nsteps < 0) return batch_fail(b, MLB_EINVAL, "nsteps must be >= 0");
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        mlb_ctx *c = b->m[i];
+        if (c->failed) return batch_fail(b, MLB_ESTATE, "member %zu is in a failed state: %s", i, c->err.c_str());
+        if (require_ready(c) != MLB_OK) return batch_fail(b, MLB_ESTATE, "member %zu: %s", i, c->err.c_str());
+    }
+    const int64_t pairs = nsteps / 2;
+    if (pairs > 0) {
+        bool stale = !b->exec;
+        for (size_t i = 0; i < b->m.size() && !stale; ++i)
+            stale = b->version[i] != b->m[i]->version || b->cur[i] != b->m[i]->cur;
+        if (stale) {
+            mlb_status st = batch_capture(b);
+            if (st != MLB_OK) return st;
+        }
+        cudaError_t e = cudaSuccess;
+        for (size_t i = 0; i < b->m.size() && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(b->pre[i], b->m[i]->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->pre[i], 0);
+        }
+        for (int64_t k = 0; k < pairs && e == cudaSuccess; ++k) e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join, b->stream);
+        for (size_t i = 0; i < b->m.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->m[i]->stream, b->join, 0);
+        if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        for (mlb_ctx *c : b->m) c->step += 2 * pairs;
+    }
+    if (nsteps % 2)
+        for (size_t i = 0; i < b->m.size(); ++i) {
+            const mlb_status st = mlb_step(b->m[i], 1);
+            if (st != MLB_OK) return batch_fail(b, st, "member %zu: %s", i, b->m[i]->err.c_str());
+        }
+    return MLB_OK;
+}
+
+mlb_status mlb_batch_synchronize(mlb_batch *b)
+{
+    if (!b) return MLB_EINVAL;
+    if (b->failed) return MLB_ESTATE;
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        const mlb_status st = mlb_synchronize(b->m[i]);
+        if (st != MLB_OK) return batch_fail(b, st, "member %zu: %s", i, b->m[i]->err.c_str());
+    }
+    return MLB_OK;
+}
+
+const char *mlb_batch_last_error(const mlb_batch *b)
+{
+    return b ? b->err.c_str() : "null batch";
+}
+
+void mlb_batch_destroy(mlb_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_fork) cudaEventDestroy(b->cap_fork);
+    if (b->join) cudaEventDestroy(b->join);
+    for (cudaEvent_t e : b->cap_done)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->pre)
+        if (e) cudaEventDestroy(e);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // extern "C"

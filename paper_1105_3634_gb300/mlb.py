@@ -91,6 +91,18 @@ def _load():
     L.mlb_kernel_name.restype = ctypes.c_char_p
     L.mlb_conservation_noalloc.argtypes = [vp, dp, ctypes.c_int32, ctypes.c_int64, vp, vp]
     L.mlb_conservation_noalloc.restype = st
+    L.mlb_autotune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.mlb_autotune.restype = st
+    L.mlb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    L.mlb_batch_create.restype = st
+    L.mlb_batch_step.argtypes = [vp, ctypes.c_int64]
+    L.mlb_batch_step.restype = st
+    L.mlb_batch_synchronize.argtypes = [vp]
+    L.mlb_batch_synchronize.restype = st
+    L.mlb_batch_last_error.argtypes = [vp]
+    L.mlb_batch_last_error.restype = ctypes.c_char_p
+    L.mlb_batch_destroy.argtypes = [vp]
+    L.mlb_batch_destroy.restype = None
     L.mlb_last_error.argtypes = [vp]
     L.mlb_last_error.restype = ctypes.c_char_p
     L.mlb_status_string.argtypes = [ctypes.c_int]
@@ -247,6 +259,14 @@ class Simulation:
         self._check(lib.mlb_set_populations(self.ctx, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                             _dp(np.ascontiguousarray(nref, np.float64)), int(step)))
 
+    def autotune(self, trials: int = 3):
+        """Pick the planes per block and the fused/split pass-2 launch by timing
+        (state and results unchanged); returns (zchunk, fused)."""
+        z = ctypes.c_int32()
+        fu = ctypes.c_int32()
+        self._check(lib.mlb_autotune(self.ctx, trials, ctypes.byref(z), ctypes.byref(fu)))
+        return z.value, bool(fu.value)
+
     def launches_per_step(self) -> int:
         return int(lib.mlb_launches_per_step(self.ctx))
 
@@ -261,3 +281,40 @@ class Simulation:
         if k < 0:
             raise MLBError(6, "profile read failed")
         return {lib.mlb_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
+
+
+class Batch:
+    """Independent Simulations stepped together through one captured CUDA
+    graph (mlb_batch_*).  The members stay usable on their own; they must
+    outlive the batch.  stream: a torch.cuda.Stream (default: one the batch
+    creates)."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.ctx.value for s in self.sims])
+        self.b = ctypes.c_void_p()
+        sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        st = lib.mlb_batch_create(arr, len(self.sims), sp, ctypes.byref(self.b))
+        if st != 0:
+            raise MLBError(st, "mlb_batch_create failed")
+
+    def _check(self, st):
+        if st != 0:
+            raise MLBError(st, lib.mlb_batch_last_error(self.b).decode() if self.b else "")
+
+    def step(self, nsteps: int):
+        self._check(lib.mlb_batch_step(self.b, nsteps))
+
+    def synchronize(self):
+        self._check(lib.mlb_batch_synchronize(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib.mlb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

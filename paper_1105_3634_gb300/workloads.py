@@ -172,3 +172,28 @@ def taylor_channel(shape=(512, 64, 64), U: float = 0.05) -> Tuple[Lattice, np.nd
     n_solv = densities_from_packing(0.211, lat.sigma[:2], [0.5, 0.5])
     n = gaussian_pulse(lat, [n_solv[0], n_solv[1], 0.0], solute=2, solute_fraction=1e-3, width=8.0)
     return lat, n
+
+
+def ensemble(count: int = 64, seed: int = 1105) -> List[Tuple[Lattice, np.ndarray]]:
+    """Independent binary systems of uneven sizes for batched runs: cubes of
+    side L in {32, 40, ..., 128}, packing 0.05 .. 0.20 (equal mole fractions,
+    sigma = (1, 1.5), tau = 1), a 5% concentration wave along x, and shear
+    U in 0 .. 0.05: U > 0.005 gives a channel between walls normal to y
+    moving at -U and +U along x (Couette), else a periodic box.  With these
+    one-site spheres the scheme stays stable to packing 0.20 between moving
+    walls (the contact layer at a wall raises the local packing to ~0.34);
+    at 0.22 with walls and at 0.25 without it does not."""
+    r = uniform01(seed, 3 * count).reshape(count, 3)
+    out = []
+    for k in range(count):
+        L = 32 + 8 * int(r[k, 0] * 13)
+        packing = 0.05 + 0.15 * r[k, 1]
+        U = 0.05 * r[k, 2]
+        if U > 0.005:
+            lat = Lattice(shape=(L, L, L), sigma=[1.0, 1.5], wall_axis=1, wall_u_lo=(-U, 0.0, 0.0),
+                          wall_u_hi=(U, 0.0, 0.0))
+        else:
+            lat = Lattice(shape=(L, L, L), sigma=[1.0, 1.5])
+        n0 = densities_from_packing(packing, lat.sigma, [0.5, 0.5])
+        out.append((lat, sine_wave(lat, n0, 0.05)))
+    return out

@@ -1,0 +1,130 @@
+"""Batched ensembles (one captured CUDA graph for many independent contexts)
+and the work-decomposition tuner: neither may change a single bit of the
+populations compared with stepping each context alone with the defaults."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1105_3634_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_3634_gb300 import build
+    build.build()
+    from paper_1105_3634_gb300 import mlb
+    return mlb
+
+
+def members():
+    """Uneven lattices and settings: the benchmark physics (fused launch),
+    a sheared channel, attraction (reach-3 tiles, split launch), three species."""
+    out = []
+    lat, n = W.binary_config1((24, 16, 12))
+    out.append((lat, n))
+    lat = W.Lattice(shape=(40, 12, 16), sigma=[1.0, 1.5], wall_axis=1, wall_u_lo=(-0.03, 0.0, 0.0),
+                    wall_u_hi=(0.03, 0.0, 0.0))
+    out.append((lat, W.noise(lat, W.densities_from_packing(0.25, lat.sigma, [0.5, 0.5]), 0.02, seed=3)))
+    out.append(W.binary_attraction((18, 16, 17), seed=4))
+    lat, n = W.taylor_channel((40, 16, 10), U=0.05)
+    n[2] = n[2] * 1e3 / 8
+    out.append((lat, n))
+    return out
+
+
+def make(gpu, torch, lat, n):
+    sim = gpu.Simulation(lat, stream=torch.cuda.Stream())
+    sim.set_fields(n, W.random_velocities(lat, 0.005, seed=11))
+    return sim
+
+
+@pytest.mark.parametrize("nsteps", [7, 10])
+def test_batch_equals_members_alone(gpu, nsteps):
+    import torch
+    cases = members()
+    alone = []
+    for lat, n in cases:
+        sim = make(gpu, torch, lat, n)
+        sim.step(nsteps)
+        alone.append(sim.populations()[0])
+        sim.close()
+    sims = [make(gpu, torch, lat, n) for lat, n in cases]
+    batch = gpu.Batch(sims)
+    batch.step(nsteps)
+    batch.synchronize()
+    for k, sim in enumerate(sims):
+        f, _, step = sim.populations()
+        assert step == nsteps
+        assert np.array_equal(f.view(np.uint32), alone[k].view(np.uint32)), k
+    batch.close()
+    for sim in sims:
+        sim.close()
+
+
+def test_batch_recaptures_after_a_settings_change(gpu):
+    """Steps 4 in the batch, then an external force on one member (its kernel
+    parameters change, so the graph must be captured again), then 4 more."""
+    import torch
+    cases = members()[:2]
+    lat0 = cases[0][0]
+    y = np.arange(lat0.nsites) // lat0.shape[0] % lat0.shape[1]
+    fext = np.zeros((lat0.nspecies, 3, lat0.nsites))
+    fext[:, 0, :] = 1e-5 * np.sin(2 * math.pi * y / lat0.shape[1])[None, :]
+
+    ref = [make(gpu, torch, lat, n) for lat, n in cases]
+    for sim in ref:
+        sim.step(4)
+    ref[0].set_external_force(fext)
+    for sim in ref:
+        sim.step(4)
+    expect = [sim.populations()[0] for sim in ref]
+
+    sims = [make(gpu, torch, lat, n) for lat, n in cases]
+    batch = gpu.Batch(sims)
+    batch.step(4)
+    batch.synchronize()
+    sims[0].set_external_force(fext)
+    batch.step(4)
+    batch.synchronize()
+    for k, sim in enumerate(sims):
+        assert np.array_equal(sim.populations()[0].view(np.uint32), expect[k].view(np.uint32)), k
+    batch.close()
+    for sim in sims + ref:
+        sim.close()
+
+
+def test_autotune_keeps_state_and_results(gpu):
+    import torch
+    for lat, n in members()[:3]:
+        a = make(gpu, torch, lat, n)
+        b = make(gpu, torch, lat, n)
+        f0 = a.populations()[0]
+        zchunk, fused = a.autotune(trials=2)
+        assert zchunk in (4, 8, 16, 32) or zchunk == lat.shape[2]
+        assert np.array_equal(a.populations()[0].view(np.uint32), f0.view(np.uint32))
+        a.step(6)
+        b.step(6)
+        assert np.array_equal(a.populations()[0].view(np.uint32), b.populations()[0].view(np.uint32))
+        a.close()
+        b.close()
+
+
+def test_batch_rejects_bad_members(gpu):
+    import torch
+    lat, n = members()[0]
+    sim = make(gpu, torch, lat, n)
+    with pytest.raises(gpu.MLBError):
+        gpu.Batch([sim, sim])                  # the same context twice
+    fresh = gpu.Simulation(lat, stream=torch.cuda.Stream())
+    batch = gpu.Batch([sim, fresh])          # fresh has no fields yet
+    with pytest.raises(gpu.MLBError, match="member 1"):
+        batch.step(2)
+    batch.close()
+    sim.close()
+    fresh.close()
