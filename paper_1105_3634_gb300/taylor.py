@@ -1,0 +1,155 @@
+"""Taylor dispersion in a periodically modulated flow (Sec. V, Eqs. ushape,
+c99, taylordiff), run through the library on the GPU.
+
+A binary mixture in a box periodic in every direction carries the steady
+shear flow u_x(y) = U cos(2 pi y / L_y), held by a body force on every
+particle, and a small concentration wave along x (Eq. perturba).  The
+section-averaged concentration C(x, t) decays as exp(-D_eff k_x^2 t) with,
+to second order in U, D_eff = D (1 + U^2 L_y^2 / (8 pi^2 D^2)) (Eq.
+taylordiff; Pe = U L_y / (2 D)).  The measurement here uses:
+
+* D: the decay rate of the same wave without flow (the lattice's own mutual
+  diffusion coefficient);
+* nu: the decay rate of a free shear wave u_x ~ cos(k_y y) (the mixture's
+  kinematic viscosity, kinetic plus collisional), which sets the force
+  F = nu k_y^2 U cos(k_y y) that holds the flow;
+* U: the cos(k_y y) amplitude of the barycentric velocity actually reached.
+
+`passive_scalar_rate` gives the exact slowest rate of the advection-diffusion
+operator for a passive scalar in this flow (all orders in U), against which
+the kinetic model's D_eff is compared; `taylor_formula` is Eq. taylordiff.
+Host-side analysis (fits, Fourier projections) only: every time step runs in
+the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Sequence, Tuple
+
+import numpy as np
+
+from . import workloads as W
+
+
+# ------------------------------------------------------------------ closed forms
+def taylor_formula(D: float, U: float, Ly: float) -> float:
+    """Eq. taylordiff: D_eff = D (1 + U^2 L_y^2 / (8 pi^2 D^2))."""
+    return D * (1.0 + U * U * Ly * Ly / (8.0 * math.pi ** 2 * D * D))
+
+
+def peclet(D: float, U: float, Ly: float) -> float:
+    """Pe = U L_y / (2 D) (Sec. V)."""
+    return U * Ly / (2.0 * D)
+
+
+def passive_scalar_rate(D: float, U: float, kx: float, ky: float, modes: int = 24) -> float:
+    """Slowest decay rate of c(x, y) = Re[sum_n a_n e^{i n ky y} e^{i kx x}]
+    under dc/dt = -u_x(y) dc/dx + D lap c with u_x = U cos(ky y): the
+    eigenvalue of the tridiagonal matrix a_n' = -D (kx^2 + n^2 ky^2) a_n
+    - i kx U (a_{n-1} + a_{n+1}) / 2, n = -modes..modes, closest to zero.
+    Returns D_eff = -rate / kx^2."""
+    n = np.arange(-modes, modes + 1)
+    A = np.diag(-D * (kx * kx + (n * ky) ** 2)).astype(complex)
+    off = -0.5j * kx * U
+    A += np.diag(np.full(2 * modes, off), 1) + np.diag(np.full(2 * modes, off), -1)
+    ev = np.linalg.eigvals(A)
+    lam = ev[np.argmax(ev.real)]
+    return float(-lam.real / (kx * kx))
+
+
+# ------------------------------------------------------------------ fields
+def cosine_flow(lat: W.Lattice, U: float) -> np.ndarray:
+    """u_x(y) = U cos(2 pi y / L_y) = -U cos(2 pi y / L_y + pi) (Eq. ushape), every species."""
+    y = W.coordinate(lat, 1)
+    u = np.zeros((lat.nspecies, 3, lat.nsites))
+    u[:, 0, :] = U * np.cos(2.0 * math.pi * y / lat.shape[1])[None, :]
+    return u
+
+
+def _mode(lat: W.Lattice, field: np.ndarray, axis: int) -> complex:
+    """Fourier amplitude of `field` [N] at the longest wavelength along `axis`
+    (all other directions averaged)."""
+    q = 2.0 * math.pi * W.coordinate(lat, axis) / lat.shape[axis]
+    return complex(np.mean(field * np.exp(-1j * q)))
+
+
+def _fit_rate(t: np.ndarray, amp: np.ndarray) -> float:
+    """Least-squares slope of -log|amp| against t."""
+    return float(-np.polyfit(t, np.log(np.abs(amp)), 1)[0])
+
+
+def _concentration(n: np.ndarray) -> np.ndarray:
+    return n[0] / (n[0] + n[1])
+
+
+# ------------------------------------------------------------------ runs on the GPU
+def _sim(mlb, lat, n, u=None, fext=None):
+    sim = mlb.Simulation(lat)
+    sim.set_fields(n, u)
+    if fext is not None:
+        sim.set_external_force(fext)
+    return sim
+
+
+def measure_viscosity(mlb, lat: W.Lattice, n0: Sequence[float], U: float = 1e-3,
+                      t0: int = 20, t1: int = 220, every: int = 20) -> float:
+    """Kinematic viscosity from the decay of a free shear wave u_x ~ cos(k_y y)
+    in the uniform mixture: nu = rate / k_y^2."""
+    n = np.array([np.full(lat.nsites, v) for v in n0])
+    sim = _sim(mlb, lat, n, cosine_flow(lat, U))
+    ts, amps = [], []
+    t = 0
+    for target in range(t0, t1 + 1, every):
+        sim.step(target - t)
+        t = target
+        nn, uu = sim.moments()
+        ub = (nn[:, None, :] * uu).sum(0) / nn.sum(0)
+        ts.append(t)
+        amps.append(_mode(lat, ub[0], 1))
+    sim.close()
+    ky = 2.0 * math.pi / lat.shape[1]
+    return _fit_rate(np.array(ts), np.array(amps)) / (ky * ky)
+
+
+def measure_dispersion(mlb, lat: W.Lattice, n0: Sequence[float], U: float, nu: float, delta: float = 0.01,
+                       t0: int = 400, t1: int = 2400, every: int = 100) -> Tuple[float, float]:
+    """(D_eff, U reached): the concentration wave n^{A,B} = n0 (1 +- delta sin(k_x x))
+    in the cosine flow held by F_x = nu k_y^2 U cos(k_y y) per particle."""
+    n = W.sine_wave(lat, n0, delta)
+    ky = 2.0 * math.pi / lat.shape[1]
+    fext = None
+    u = None
+    if U != 0.0:
+        u = cosine_flow(lat, U)
+        fext = np.zeros((lat.nspecies, 3, lat.nsites))
+        fext[:, 0, :] = nu * ky * ky * u[:, 0, :]
+    sim = _sim(mlb, lat, n, u, fext)
+    ts, amps, flows = [], [], []
+    t = 0
+    for target in range(t0, t1 + 1, every):
+        sim.step(target - t)
+        t = target
+        nn, uu = sim.moments()
+        ts.append(t)
+        amps.append(_mode(lat, _concentration(nn), 0))
+        ub = (nn[:, None, :] * uu).sum(0) / nn.sum(0)
+        flows.append(2.0 * abs(_mode(lat, ub[0], 1)))
+    sim.close()
+    kx = 2.0 * math.pi / lat.shape[0]
+    return _fit_rate(np.array(ts), np.array(amps)) / (kx * kx), float(np.mean(flows))
+
+
+def dispersion_curve(mlb, lat: W.Lattice, n0: Sequence[float], Us: Sequence[float], **kw) -> Dict:
+    """D(0), nu, and for every U: the measured D_eff, the flow reached, Pe, the
+    exact passive-scalar D_eff and Eq. taylordiff."""
+    D0, _ = measure_dispersion(mlb, lat, n0, 0.0, 0.0, **kw)
+    nu = measure_viscosity(mlb, lat, n0)
+    kx = 2.0 * math.pi / lat.shape[0]
+    ky = 2.0 * math.pi / lat.shape[1]
+    rows = []
+    for U in Us:
+        Deff, Ur = measure_dispersion(mlb, lat, n0, U, nu, **kw)
+        rows.append({"U": U, "U_reached": Ur, "Pe": peclet(D0, Ur, lat.shape[1]), "D_eff": Deff,
+                     "D_eff_passive_scalar": passive_scalar_rate(D0, Ur, kx, ky),
+                     "D_eff_eq_taylordiff": taylor_formula(D0, Ur, lat.shape[1])})
+    return {"D0": D0, "nu": nu, "rows": rows}
