@@ -40,10 +40,12 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mlb", "reference"], default="mlb")
     ap.add_argument("--size", type=int, default=None, help="cubic lattice extent (default: the workload's)")
-    ap.add_argument("--workload", choices=["binary", "attraction", "ensemble"], default="binary",
+    ap.add_argument("--workload", choices=["binary", "attraction", "ensemble", "surrogate"], default="binary",
                     help="binary: sigma 1/1.5 packing 0.2 (256^3); attraction: sigma 2/3, eps kT/2 tails, "
                          "packing 0.3, 1%% noise (128^3); ensemble: 64 independent binary systems of "
-                         "32^3..128^3, packing 0.05-0.20, shear 0-0.05, stepped as one captured graph")
+                         "32^3..128^3, packing 0.05-0.20, shear 0-0.05, stepped as one captured graph; "
+                         "surrogate: the binary workload with the learned hard-core force (trained first on "
+                         "64x8x8 frames, exact recheck every 50 steps, bound 5%%), timed against the exact step")
     ap.add_argument("--members", type=int, default=64, help="ensemble size")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the default decomposition")
     ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample extent for cpu_baseline")
@@ -52,7 +54,7 @@ def parse_args():
     return ap.parse_args()
 
 
-DEFAULT_SIZE = {"binary": 256, "attraction": 128, "ensemble": 0}
+DEFAULT_SIZE = {"binary": 256, "attraction": 128, "ensemble": 0, "surrogate": 256}
 
 
 def workload(size, kind="binary"):
@@ -64,6 +66,8 @@ def workload(size, kind="binary"):
 
 def config_dict(size, kind="binary"):
     desc = {"binary": "binary hard spheres sigma=(1,1.5), packing 0.2, tau=1, 5% sine wave",
+            "surrogate": "binary hard spheres sigma=(1,1.5), packing 0.2, tau=1, 5% sine wave, hard-core force "
+                         "from the learned surrogate (exact recheck every 50 steps, bound 5%)",
             "attraction": "binary sigma=(2,3), attractive tails -eps(sigma/r)^6 to 2.5 sigma, eps=kT/2, "
                           "packing 0.3, 1% noise, tau=1"}[kind]
     return {"workload": f"{desc}, {size}^3 periodic D3Q19",
@@ -135,6 +139,8 @@ def attraction_points(lat):
 #   attraction: one 3-vector multiply-add per point of the full region (6)
 FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18, "k_pass2_collide": 18}
 FLOPS_PER_ATTRACTION_POINT = 6
+# the surrogate network per site: 3^3 conv 2->32, 3^3 conv 32->32 (tensor cores), 1^3 conv 32->6
+FLOPS_PER_SURROGATE_SITE = 2 * (27 * 2 * 32 + 27 * 32 * 32 + 32 * 6)
 
 
 def fp32_peak_tflops(sm_mhz=2070.0):
@@ -143,7 +149,7 @@ def fp32_peak_tflops(sm_mhz=2070.0):
 
 
 KERNEL_SOURCE = {"k_pass1": "mlb_pass1.cu", "k_pass2": "mlb_pass2.cu", "k_pass2_collide": "mlb_pass2.cu",
-                 "k_attraction": "mlb_attraction.cu"}
+                 "k_attraction": "mlb_attraction.cu", "k_surrogate": "mlb_surrogate.cu"}
 
 
 def kernel_source_sha(kernel):
@@ -201,6 +207,15 @@ def measured_peak_hbm():
             return float(json.load(fh)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def measured_peak_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 # ------------------------------------------------------------------ clocks
@@ -290,6 +305,9 @@ def run_mlb(args, rank, world, local_rank):
     sim.set_fields(n)
     sim.step(args.warmup)
     sim.synchronize()
+    surrogate = None
+    if args.workload == "surrogate":
+        surrogate = run_surrogate_setup(args, mlb, sim, lat, stream)
 
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -366,6 +384,9 @@ def run_mlb(args, rank, world, local_rank):
             fl = FLOPS_PER_ATTRACTION_POINT * attraction_points(lat) * N
             k["flops_note"] = ("direct lattice sum, one 3-vector FMA per region point; the column kernel "
                                "executes about 1.25 FP32 flops per point through K(-d) = -K(d)")
+        elif name == "k_surrogate":
+            fl = FLOPS_PER_SURROGATE_SITE * N
+            k["flops_note"] = "dense network flops; the 32->32 layer (94% of them) on BF16 tensor cores"
         if fl is not None:
             k["algorithmic_flops_per_launch"] = fl
             k["achieved_tflops"] = fl / (per_launch_ms * 1e-3) / 1e12
@@ -384,22 +405,67 @@ def run_mlb(args, rank, world, local_rank):
            "traffic": committed_traffic(top, args.size, args.workload)}
     # the binding resource of the dominant kernel: the larger fraction of its peak
     roof = alu if (alu["frac"] or 0.0) > (hbm["frac"] or 0.0) else hbm
+    if top == "k_surrogate":
+        tpk = measured_peak_bf16()
+        roof = {"kernel": top, "bound": "tensor", "achieved": kt["achieved_tflops"], "peak": tpk,
+                "peak_kind": "measured (MEASURED_PEAKS.json bf16_tflops, burst)", "unit": "TFLOP/s",
+                "frac": kt["achieved_tflops"] / tpk, "traffic": committed_traffic(top, args.size, args.workload)}
     step_bytes = 184.0 * S * N
     step_roof = {"bytes_per_species_site": 184, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
                  "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "peak_gbs": peak}
 
+    if surrogate is not None:
+        net = surrogate.pop("net")
+        active, last, rechecks, rejections = sim.surrogate_status()
+        surrogate.update({"ms_per_step": ms_step, "speedup_vs_exact": surrogate["ms_per_step_exact"] / ms_step,
+                          "active_at_end": active, "last_recheck_error": last, "rechecks": rechecks,
+                          "rejections": rejections})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sine-wave mixture)",
            "config": config_dict(args.size, args.workload), "roofline": roof, "step_roofline": step_roof,
            "kernels": kernels, "gpu_launches": sim.launches_per_step() * args.steps * 1,
            "mlups": value / S, "clocks": clk, "e2e": e2e}
+    if surrogate is not None:
+        out["surrogate"] = surrogate
+        out["dtype"] = "f32 step, bf16 network activations (fp32 input and accumulation)"
     sim.close()
+    if surrogate is not None:
+        net.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample if args.workload == "binary" else 48, args.workload)
     if dist:
         dist.destroy_process_group()
     return out
+
+
+def run_surrogate_setup(args, mlb, sim, lat, stream):
+    """Train the surrogate (64x8x8 frames, stencil start, GPU fine-tuning), time
+    the exact step on `sim` over the same number of steps, then attach the
+    network; the caller's timed region then measures the surrogate step."""
+    import torch
+    from paper_1105_3634_gb300 import surrogate as SG
+    t0 = time.perf_counter()
+    params, ins, outs, _ = SG.recipe(mlb)
+    train_s = time.perf_counter() - t0
+    net = mlb.Net(lat.shape)
+    net.set_params(params)
+    net.set_scales(ins, outs)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sim.synchronize()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    sim.synchronize()
+    ms_exact = e0.elapsed_time(e1) / args.steps
+    sim.attach_surrogate(net, recheck_every=50, bound=0.05)
+    sim.step(args.warmup)
+    sim.synchronize()
+    return {"net": net, "ms_per_step_exact": ms_exact, "recheck_every": 50, "bound": 0.05,
+            "training": "240 frames on 64x8x8, least-squares linear-response start, 100 epochs of Adam "
+                        "on the GPU (lr 1e-6 cosine)", "training_s": train_s,
+            "exact_timing": "same lattice and stream, the same number of steps just before, CUDA events"}
 
 
 def run_ensemble(args, rank, world, local_rank):

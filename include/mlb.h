@@ -198,6 +198,65 @@ mlb_status mlb_batch_synchronize(mlb_batch *batch);
 const char *mlb_batch_last_error(const mlb_batch *batch);
 void mlb_batch_destroy(mlb_batch *batch);
 
+/* The rest force of pass 1 at the current state, F^hc + G + F_ext per
+ * particle (Eq. potmeanforce without the velocity exchange), as FP64
+ * force[S][3][N] on the host.  Synchronous.  Without tails and external
+ * force it is the hard-core force alone: the training target of the
+ * surrogate below. */
+mlb_status mlb_get_rest_force(mlb_ctx *ctx, double *force);
+
+/* Learned surrogate of the hard-core force (no counterpart in the paper; the
+ * exact force stays as the reference).  A 3-layer 3D convolutional network
+ * for binary mixtures on a periodic lattice: input (n^a - n_ref^a) in_scale_a
+ * (2 channels), 3^3 convolutions to 32 and 32 channels with tanh, a 1^3
+ * convolution to 6 outputs = F^a_i out_scale_a (a 5^3 receptive field).
+ * The biases are part of the layout but training keeps them at zero (the
+ * network is odd in its input, as the hard-core force is at linear order).
+ * FP32 input, BF16 hidden activations, FP32 accumulation; the 32 -> 32 layer on the tensor
+ * cores.  Parameters: mlb_net_param_count() FP32 values, layout
+ * W1[27][32][2] b1[32] W2[27][32][32] b2[32] W3[6][32] b3[6] with
+ * W[tap][out][in], tap = (dz+1)*9 + (dy+1)*3 + (dx+1).  The net owns its
+ * device memory and stream; host arrays are the caller's and are copied.
+ *   create: dims = (nx, ny, nz) of the lattices it will serve, each >= 3;
+ *           parameters start at zero.
+ *   forward: dn [2][N] -> force [2][3][N] (FP64 host arrays).
+ *   gradient: loss = sum (net - t)^2 / sum t^2 over the 6N entries, with
+ *           t = force out_scale (the squared relative force error; force must
+ *           not vanish everywhere), and its gradient grad[param_count]
+ *           (either output may be NULL).
+ *   train:  `iters` Adam steps (beta 0.9 / 0.999) on one frame; loss of the
+ *           last step.  Only the weights move: the biases keep the values
+ *           last set (zero keeps the network odd in its input).
+ * Errors: MLB_EINVAL (bad arguments, non-finite parameters or scales),
+ * MLB_ENOMEM, MLB_ECUDA (mlb_net_last_error gives the message). */
+typedef struct mlb_net mlb_net;
+int64_t mlb_net_param_count(void);
+mlb_status mlb_net_create(const int32_t *dims, mlb_net **out);
+mlb_status mlb_net_set_params(mlb_net *net, const float *params);
+mlb_status mlb_net_get_params(mlb_net *net, float *params);
+mlb_status mlb_net_set_scales(mlb_net *net, const double *in_scale, const double *out_scale);
+mlb_status mlb_net_forward(mlb_net *net, const double *dn, double *force);
+mlb_status mlb_net_gradient(mlb_net *net, const double *dn, const double *force, float *grad, double *loss);
+mlb_status mlb_net_train(mlb_net *net, const double *dn, const double *force, int32_t iters, double lr,
+                         double *loss);
+const char *mlb_net_last_error(const mlb_net *net);
+void mlb_net_destroy(mlb_net *net);
+
+/* Use the surrogate for the hard-core force in mlb_step (net = NULL detaches
+ * it).  Binary, periodic, no tails, no drag-only mode, contact shells of
+ * reach <= 2, the net's dims equal to the lattice's.  While it is active,
+ * pass 1 skips the hard-core sums and takes the network's force; every
+ * `recheck_every` >= 1 steps the step runs with the exact force instead and
+ * compares: if the relative 2-norm error of the network's force exceeds
+ * `bound` the surrogate is switched off for good (the exact force is the
+ * fallback).  The net must outlive the attachment.  mlb_surrogate_status
+ * reports whether it is active, the last measured error (-1 before the first
+ * recheck), and the numbers of rechecks and rejections (any pointer may be
+ * NULL). */
+mlb_status mlb_attach_surrogate(mlb_ctx *ctx, mlb_net *net, int32_t recheck_every, double bound);
+mlb_status mlb_surrogate_status(mlb_ctx *ctx, int32_t *active, double *last_error, int64_t *rechecks,
+                                int64_t *rejections);
+
 /* Conservation sums without any allocation (the paper has no counterpart:
  * this serves callers that cannot let the library allocate).  A caller whose
  * device memory is all owned by its own memory manager (a framework pool, a

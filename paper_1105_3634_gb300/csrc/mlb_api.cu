@@ -52,6 +52,13 @@ struct mlb_ctx {
     int tuned_split = -1;
     // bumped whenever the kernels' parameters change (captured graphs go stale)
     uint64_t version = 0;
+    // learned surrogate of the hard-core force (mlb_attach_surrogate)
+    mlb_net *surr = nullptr;
+    int surr_every = 0;
+    double surr_bound = 0.0, surr_err = -1.0;
+    bool surr_active = false;
+    int64_t surr_rechecks = 0, surr_rejections = 0;
+    double *surr_sums = nullptr;                // device [2]
 };
 
 namespace {
@@ -357,10 +364,10 @@ mlb_status require_ready(mlb_ctx *c)
 
 enum {
     K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_ATTRACTION = 5, K_PASS2_COLLIDE = 6,
-    K_NKINDS = 7
+    K_SURROGATE = 7, K_NKINDS = 8
 };
 const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2", "k_collide",
-                                            "k_attraction", "k_pass2_collide"};
+                                            "k_attraction", "k_pass2_collide", "k_surrogate"};
 
 // event pair around one launch when profiling
 struct Timed {
@@ -400,6 +407,31 @@ mlb_status forces(mlb_ctx *c)
     if (c->p.attr_r) {
         Timed t(c, K_ATTRACTION);
         MLB_CUDA(c, mlbi_launch_attraction(c->p, c->b, c->stream));
+    }
+    if (c->surr && c->surr_active) {
+        // the network's F^hc into attr; every surr_every steps the exact pass 1
+        // runs instead and the network is checked against it
+        { Timed t(c, K_SURROGATE); MLB_CUDA(c, mlbi_net_force_from_moments(c->surr, c->b.mom, c->b.attr, c->stream)); }
+        if (c->step % c->surr_every != 0) {
+            mlbi_params q = c->p;
+            q.hc_from_attr = 1;
+            Timed t(c, K_PASS1);
+            MLB_CUDA(c, mlbi_launch_pass1(q, c->b, c->stream));
+            return MLB_OK;
+        }
+        { Timed t(c, K_PASS1); MLB_CUDA(c, mlbi_launch_pass1(c->p, c->b, c->stream)); }
+        double sums[2] = {0.0, 0.0};
+        MLB_CUDA(c, mlbi_force_error((long long)c->p.S * c->p.N, c->b.attr, c->b.frest, c->surr_sums, c->stream));
+        MLB_CUDA(c, cudaMemcpyAsync(sums, c->surr_sums, sizeof sums, cudaMemcpyDeviceToHost, c->stream));
+        MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->surr_err = sums[1] > 0.0 ? std::sqrt(sums[0] / sums[1]) : (sums[0] > 0.0 ? 1.0 : 0.0);
+        ++c->surr_rechecks;
+        if (!(c->surr_err <= c->surr_bound)) {
+            c->surr_active = false;
+            ++c->surr_rejections;
+            ++c->version;
+        }
+        return MLB_OK;
     }
     { Timed t(c, K_PASS1); MLB_CUDA(c, mlbi_launch_pass1(c->p, c->b, c->stream)); }
     return MLB_OK;
@@ -715,7 +747,8 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;
-    return (c->p.local_g ? 1 : 2) + (split_collide(c) ? 3 : 2) + (c->p.attr_r ? 1 : 0);
+    return (c->p.local_g ? 1 : 2) + (split_collide(c) ? 3 : 2) + (c->p.attr_r ? 1 : 0) +
+           (c->surr && c->surr_active ? 4 : 0);
 }
 
 const char *mlb_kernel_name(int32_t k)
@@ -929,8 +962,71 @@ void mlb_destroy(mlb_ctx *c)
         else cudaFree(c->slab);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->surr_sums) cudaFree(c->surr_sums);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+mlb_status mlb_get_rest_force(mlb_ctx *c, double *force)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    if (!force) return fail(c, MLB_EINVAL, "force is required");
+    const bool active = c->surr_active, prof = c->profiling;
+    c->surr_active = false;                      // the exact force
+    c->profiling = false;
+    st = forces(c);
+    c->surr_active = active;
+    c->profiling = prof;
+    if (st != MLB_OK) return st;
+    const size_t bytes = sizeof(double) * 3 * c->p.S * c->p.N;
+    MLB_CUDA(c, mlbi_launch_export_vec(c->p, c->b.frest, c->b.stage, c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(force, c->b.stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_flags(c);
+}
+
+mlb_status mlb_attach_surrogate(mlb_ctx *c, mlb_net *net, int32_t recheck_every, double bound)
+{
+    MLB_GUARD(c);
+    if (!net) {
+        c->surr = nullptr;
+        c->surr_active = false;
+        ++c->version;
+        return MLB_OK;
+    }
+    if (!c->species_set) return fail(c, MLB_ESTATE, "call mlb_set_species first");
+    if (c->p.S != 2) return fail(c, MLB_EINVAL, "the surrogate serves binary mixtures");
+    if (c->desc.wall_axis != -1) return fail(c, MLB_EINVAL, "the surrogate serves periodic lattices");
+    if (c->p.has_attraction) return fail(c, MLB_EINVAL, "the surrogate replaces the hard core only: no tails");
+    if (c->p.drag_only) return fail(c, MLB_EINVAL, "the surrogate needs the default velocity exchange");
+    if (c->p.tile_r != 1 && c->p.tile_r != 2)
+        return fail(c, MLB_EINVAL, "contact shells of reach %d exceed the network's 5^3 field", c->p.tile_r);
+    if (!mlbi_net_matches(net, c->desc.nx, c->desc.ny, c->desc.nz))
+        return fail(c, MLB_EINVAL, "the network was created for another lattice size");
+    if (recheck_every < 1 || !(bound > 0.0) || !std::isfinite(bound))
+        return fail(c, MLB_EINVAL, "recheck_every must be >= 1 and bound > 0");
+    if (!c->surr_sums) MLB_CUDA(c, cudaMalloc(&c->surr_sums, 2 * sizeof(double)));
+    c->surr = net;
+    c->surr_every = recheck_every;
+    c->surr_bound = bound;
+    c->surr_active = true;
+    c->surr_err = -1.0;
+    c->surr_rechecks = c->surr_rejections = 0;
+    ++c->version;
+    return MLB_OK;
+}
+
+mlb_status mlb_surrogate_status(mlb_ctx *c, int32_t *active, double *last_error, int64_t *rechecks,
+                                int64_t *rejections)
+{
+    if (!c) return MLB_EINVAL;
+    if (active) *active = (c->surr && c->surr_active) ? 1 : 0;
+    if (last_error) *last_error = c->surr_err;
+    if (rechecks) *rechecks = c->surr_rechecks;
+    if (rejections) *rejections = c->surr_rejections;
+    return MLB_OK;
 }
 
 }  // extern "C"
@@ -971,6 +1067,9 @@ mlb_status batch_capture(mlb_batch *b)
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
+    for (size_t i = 0; i < b->m.size(); ++i)
+        if (b->m[i]->surr && b->m[i]->surr_active)
+            return batch_fail(b, MLB_EINVAL, "member %zu uses a surrogate (its rechecks read back to the host)", i);
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
     mlb_status st = MLB_OK;

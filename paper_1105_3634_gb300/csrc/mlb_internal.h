@@ -69,6 +69,7 @@ struct mlbi_params {
     // (k, dz k) per (column, pair, dz = 0..attr_r) at ((float2 *)(table + aw_start))
     int acol_start, acol_count, aw_start;
     int zchunk;                      // planes per block of the tiled kernels
+    int hc_from_attr;                // 1: pass 1 skips the hard-core sums and takes attr as F^hc (surrogate)
     int pair_index[MLBI_MAXS][MLBI_MAXS];
     mlbi_pair pair[MLBI_MAXP];
     float wall_lo[3], wall_hi[3];
@@ -133,3 +134,13 @@ cudaError_t mlbi_launch_export_moments(const mlbi_params &p, const mlbi_buffers 
 cudaError_t mlbi_launch_import_fext(const mlbi_params &p, const mlbi_buffers &b, const double *fext,
                                     cudaStream_t s);
 cudaError_t mlbi_launch_conservation(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
+// float4 [S][N] (x, y, z) -> FP64 [S][3][N]
+cudaError_t mlbi_launch_export_vec(const mlbi_params &p, const float4 *src, double *dst, cudaStream_t s);
+
+// learned surrogate of the hard-core force (mlb_surrogate.cu)
+struct mlb_net;
+bool mlbi_net_matches(const mlb_net *n, int nx, int ny, int nz);
+// force[S][N] = the network's F^hc from the moments' n - n_ref
+cudaError_t mlbi_net_force_from_moments(mlb_net *n, const float4 *mom, float4 *force, cudaStream_t s);
+// sums[0] = sum |fs - fx|^2, sums[1] = sum |fx|^2 over n4 float4 (x, y, z)
+cudaError_t mlbi_force_error(long long n4, const float4 *fs, const float4 *fx, double *sums, cudaStream_t s);

@@ -279,6 +279,27 @@ cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cuda
     default: return cudaErrorInvalidValue;                                                         \
     }
 
+namespace {
+__global__ void __launch_bounds__(kBlock) k_export_vec(mlbi_params p, const float4 *__restrict__ src,
+                                                       double *__restrict__ dst)
+{
+    const long long N = p.N;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x)
+        for (int a = 0; a < p.S; ++a) {
+            const float4 v = src[a * N + r];
+            dst[(a * 3 + 0) * N + r] = v.x;
+            dst[(a * 3 + 1) * N + r] = v.y;
+            dst[(a * 3 + 2) * N + r] = v.z;
+        }
+}
+}  // namespace
+
+cudaError_t mlbi_launch_export_vec(const mlbi_params &p, const float4 *src, double *dst, cudaStream_t s)
+{
+    k_export_vec<<<grid_for(p.N), kBlock, 0, s>>>(p, src, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
 {
     MLBI_DISPATCH_S((k_moments_g<SS><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags)));

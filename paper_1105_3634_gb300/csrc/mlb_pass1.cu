@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass1(const mlbi_params p, const 
 
 // ------------------------------------------------------------------ tiled variants
 // Shell sums from the tile with the stencil table (same sums as pass1_shells).
-template <int S, int R, bool DRAG, int TY>
+template <int S, int R, bool DRAG, int TY, bool HC>
 __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
                                                   const float4 *sf, const float *sg, int kz, int cidx,
                                                   const Centre<S> &c, const PairW<S> &w, Acc1<S> &A)
@@ -223,7 +223,7 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
                 float t, sd, wn;
                 pass1_point<DRAG>(np, nm, dd, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre, w.h[q],
                                   -0.5f * p.pair[q].hc_pre, sdu, t, sd, wn);
-                add_pass1(sx, sy, sz, t, sd, wn, A.hc[a], A.fv[a], A.G[a]);
+                add_pass1(sx, sy, sz, HC ? t : 0.f, sd, wn, A.hc[a], A.fv[a], A.G[a]);
             }
         }
     }
@@ -234,7 +234,7 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
 // classes of each pair's shell.  The +-d data of a class is read once per
 // neighbour species and shared by every species a.  f[3], g[3]: element
 // offsets of the planes z - 1, z, z + 1 of the float4 and dg tiles.
-template <int S, bool DRAG, int CL>
+template <int S, bool DRAG, int CL, bool HC>
 __device__ __forceinline__ void pass1_cube_class(const mlbi_params &p, const float4 *sf, const float *sg, int b,
                                                  const int (&f)[3], const int (&g)[3], const Centre<S> &c,
                                                  const PairW<S> &w, Acc1<S> &A)
@@ -271,14 +271,14 @@ __device__ __forceinline__ void pass1_cube_class(const mlbi_params &p, const flo
             float t, sd, wn;
             pass1_point<DRAG>(np, nm, dd, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre, w.h[q],
                               -0.5f * p.pair[q].hc_pre, sdu, t, sd, wn);
-            cube_add<k>(il, t, A.hc[a]);
+            if constexpr (HC) cube_add<k>(il, t, A.hc[a]);
             cube_add<k>(il, sd, A.fv[a]);
             cube_add_ss<k>(il, wn, A.G[a]);
         }
     });
 }
 
-template <int S, bool DRAG>
+template <int S, bool DRAG, bool HC>
 __device__ __forceinline__ void pass1_cube(const mlbi_params &p, const float4 *sf, const float *sg, int kz, int cidx,
                                            const Centre<S> &c, const PairW<S> &w, Acc1<S> &A)
 {
@@ -289,13 +289,14 @@ __device__ __forceinline__ void pass1_cube(const mlbi_params &p, const float4 *s
                       ring(kz + 1, T::NSLOT) * T::NP * T::PLANE + cidx};
 #pragma unroll
     for (int b = 0; b < S; ++b) {
-        pass1_cube_class<S, DRAG, 0>(p, sf, sg, b, f, g, c, w, A);
-        pass1_cube_class<S, DRAG, 1>(p, sf, sg, b, f, g, c, w, A);
-        pass1_cube_class<S, DRAG, 2>(p, sf, sg, b, f, g, c, w, A);
+        pass1_cube_class<S, DRAG, 0, HC>(p, sf, sg, b, f, g, c, w, A);
+        pass1_cube_class<S, DRAG, 1, HC>(p, sf, sg, b, f, g, c, w, A);
+        pass1_cube_class<S, DRAG, 2, HC>(p, sf, sg, b, f, g, c, w, A);
     }
 }
 
-template <int S, int R, bool DRAG, int TY>
+// HC = false: the hard-core sums are left out and attr holds F^hc (the learned surrogate's)
+template <int S, int R, bool DRAG, int TY, bool HC>
 __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S <= 2 ? 6 : 2))
     k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom, const float *__restrict__ dg,
                   const mlbi_entry *__restrict__ tab, const float4 *__restrict__ fext, const float4 *__restrict__ attr,
@@ -342,10 +343,10 @@ __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S
         pair_weights<S>(p, dgc, w);
         Acc1<S> A;
         A.zero();
-        if constexpr (R == 1 && TY == kBY) pass1_cube<S, DRAG>(p, sf, sg, kz, cidx, c, w, A);
-        else pass1_tile_shells<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, c, w, A);
+        if constexpr (R == 1 && TY == kBY) pass1_cube<S, DRAG, HC>(p, sf, sg, kz, cidx, c, w, A);
+        else pass1_tile_shells<S, R, DRAG, TY, HC>(p, tab, sf, sg, kz, cidx, c, w, A);
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
-        if (p.attr_r) {
+        if (!HC || p.attr_r) {
 #pragma unroll
             for (int a = 0; a < S; ++a) {
                 const float4 v = attr[a * p.N + r];
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S
     }
 }
 
-template <int S, int R, bool DRAG>
+template <int S, int R, bool DRAG, bool HC = true>
 cudaError_t launch_pass1_tiled(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
 {
     constexpr int TY = mlbi_tile_ty(S, R);
@@ -371,7 +372,7 @@ cudaError_t launch_pass1_tiled(const mlbi_params &p, const mlbi_buffers &b, cuda
         return cudaErrorInvalidValue;
     } else {
         using T = Tile<S, R, TY>;
-        auto k = k_pass1_tiled<S, R, DRAG, TY>;
+        auto k = k_pass1_tiled<S, R, DRAG, TY, HC>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
         if (e != cudaSuccess) return e;
         const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + TY - 1) / TY),
@@ -384,6 +385,14 @@ cudaError_t launch_pass1_tiled(const mlbi_params &p, const mlbi_buffers &b, cuda
 template <int S, bool DRAG>
 cudaError_t launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
 {
+    if (p.hc_from_attr) {
+        // the surrogate's case only: binary, no drag-only mode, reach 1 or 2
+        if constexpr (S == 2 && !DRAG) {
+            if (p.tile_r == 1) return launch_pass1_tiled<S, 1, DRAG, false>(p, b, s);
+            if (p.tile_r == 2) return launch_pass1_tiled<S, 2, DRAG, false>(p, b, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (p.tile_r == 1) return launch_pass1_tiled<S, 1, DRAG>(p, b, s);
     if (p.tile_r == 2) return launch_pass1_tiled<S, 2, DRAG>(p, b, s);
     if (p.tile_r == 3) return launch_pass1_tiled<S, 3, DRAG>(p, b, s);

@@ -103,6 +103,33 @@ def _load():
     L.mlb_batch_last_error.restype = ctypes.c_char_p
     L.mlb_batch_destroy.argtypes = [vp]
     L.mlb_batch_destroy.restype = None
+    L.mlb_get_rest_force.argtypes = [vp, dp]
+    L.mlb_get_rest_force.restype = st
+    L.mlb_net_param_count.argtypes = []
+    L.mlb_net_param_count.restype = ctypes.c_int64
+    L.mlb_net_create.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vp)]
+    L.mlb_net_create.restype = st
+    L.mlb_net_set_params.argtypes = [vp, fp]
+    L.mlb_net_set_params.restype = st
+    L.mlb_net_get_params.argtypes = [vp, fp]
+    L.mlb_net_get_params.restype = st
+    L.mlb_net_set_scales.argtypes = [vp, dp, dp]
+    L.mlb_net_set_scales.restype = st
+    L.mlb_net_forward.argtypes = [vp, dp, dp]
+    L.mlb_net_forward.restype = st
+    L.mlb_net_gradient.argtypes = [vp, dp, dp, fp, dp]
+    L.mlb_net_gradient.restype = st
+    L.mlb_net_train.argtypes = [vp, dp, dp, ctypes.c_int32, ctypes.c_double, dp]
+    L.mlb_net_train.restype = st
+    L.mlb_net_last_error.argtypes = [vp]
+    L.mlb_net_last_error.restype = ctypes.c_char_p
+    L.mlb_net_destroy.argtypes = [vp]
+    L.mlb_net_destroy.restype = None
+    L.mlb_attach_surrogate.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double]
+    L.mlb_attach_surrogate.restype = st
+    L.mlb_surrogate_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), dp, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]
+    L.mlb_surrogate_status.restype = st
     L.mlb_last_error.argtypes = [vp]
     L.mlb_last_error.restype = ctypes.c_char_p
     L.mlb_status_string.argtypes = [ctypes.c_int]
@@ -259,6 +286,29 @@ class Simulation:
         self._check(lib.mlb_set_populations(self.ctx, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                             _dp(np.ascontiguousarray(nref, np.float64)), int(step)))
 
+    def rest_force(self):
+        """F^hc + G + F_ext at the current state, [S][3][N] (mlb_get_rest_force)."""
+        f = np.empty((self.S, 3, self.N))
+        self._check(lib.mlb_get_rest_force(self.ctx, _dp(f)))
+        return f
+
+    def attach_surrogate(self, net, recheck_every: int = 50, bound: float = 0.05):
+        """Take the hard-core force from `net` (a Net; None detaches it); every
+        `recheck_every` steps the exact force is used and compared, and a
+        relative 2-norm error above `bound` detaches the network for good."""
+        self._surrogate = net
+        self._check(lib.mlb_attach_surrogate(self.ctx, net.n if net is not None else None, recheck_every, bound))
+
+    def surrogate_status(self):
+        """(active, last relative error, rechecks, rejections)."""
+        a = ctypes.c_int32()
+        e = ctypes.c_double()
+        rc = ctypes.c_int64()
+        rj = ctypes.c_int64()
+        self._check(lib.mlb_surrogate_status(self.ctx, ctypes.byref(a), ctypes.byref(e), ctypes.byref(rc),
+                                             ctypes.byref(rj)))
+        return bool(a.value), e.value, rc.value, rj.value
+
     def autotune(self, trials: int = 3):
         """Pick the planes per block and the fused/split pass-2 launch by timing
         (state and results unchanged); returns (zchunk, fused)."""
@@ -312,6 +362,75 @@ class Batch:
         if getattr(self, "b", None):
             lib.mlb_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """The learned hard-core force (mlb_net_*) for lattices of shape dims:
+    3D convolutions 2 -> 32 -> 32 -> 6, BF16 activations, FP32 accumulation."""
+
+    def __init__(self, dims):
+        d = (ctypes.c_int32 * 3)(*[int(v) for v in dims])
+        self.dims = tuple(int(v) for v in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.n = ctypes.c_void_p()
+        st = lib.mlb_net_create(d, ctypes.byref(self.n))
+        if st != 0:
+            raise MLBError(st, "mlb_net_create failed")
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib.mlb_net_param_count())
+
+    def _check(self, st):
+        if st != 0:
+            raise MLBError(st, lib.mlb_net_last_error(self.n).decode() if self.n else "")
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.param_count()
+        self._check(lib.mlb_net_set_params(self.n, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def params(self):
+        p = np.empty(self.param_count(), np.float32)
+        self._check(lib.mlb_net_get_params(self.n, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    def set_scales(self, in_scale, out_scale):
+        self._check(lib.mlb_net_set_scales(self.n, _dp(np.ascontiguousarray(in_scale, np.float64)),
+                                           _dp(np.ascontiguousarray(out_scale, np.float64))))
+
+    def forward(self, dn):
+        dn = np.ascontiguousarray(dn, np.float64).reshape(2, self.N)
+        f = np.empty((2, 3, self.N))
+        self._check(lib.mlb_net_forward(self.n, _dp(dn), _dp(f)))
+        return f
+
+    def gradient(self, dn, force):
+        dn = np.ascontiguousarray(dn, np.float64).reshape(2, self.N)
+        force = np.ascontiguousarray(force, np.float64).reshape(2, 3, self.N)
+        g = np.empty(self.param_count(), np.float32)
+        loss = ctypes.c_double()
+        self._check(lib.mlb_net_gradient(self.n, _dp(dn), _dp(force), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         ctypes.byref(loss)))
+        return loss.value, g
+
+    def train(self, dn, force, iters: int, lr: float) -> float:
+        dn = np.ascontiguousarray(dn, np.float64).reshape(2, self.N)
+        force = np.ascontiguousarray(force, np.float64).reshape(2, 3, self.N)
+        loss = ctypes.c_double()
+        self._check(lib.mlb_net_train(self.n, _dp(dn), _dp(force), iters, lr, ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "n", None):
+            lib.mlb_net_destroy(self.n)
+            self.n = None
 
     def __del__(self):
         try:
