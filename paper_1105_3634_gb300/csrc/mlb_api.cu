@@ -424,6 +424,7 @@ mlb_status forces(mlb_ctx *c)
         MLB_CUDA(c, mlbi_force_error((long long)c->p.S * c->p.N, c->b.attr, c->b.frest, c->surr_sums, c->stream));
         MLB_CUDA(c, cudaMemcpyAsync(sums, c->surr_sums, sizeof sums, cudaMemcpyDeviceToHost, c->stream));
         MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (mlbi_net_timed_out(c->surr)) return fail(c, MLB_ETIMEOUT, "the surrogate's tensor-core kernel gave up a wait");
         c->surr_err = sums[1] > 0.0 ? std::sqrt(sums[0] / sums[1]) : (sums[0] > 0.0 ? 1.0 : 0.0);
         ++c->surr_rechecks;
         if (!(c->surr_err <= c->surr_bound)) {

@@ -140,6 +140,8 @@ cudaError_t mlbi_launch_export_vec(const mlbi_params &p, const float4 *src, doub
 // learned surrogate of the hard-core force (mlb_surrogate.cu)
 struct mlb_net;
 bool mlbi_net_matches(const mlb_net *n, int nx, int ny, int nz);
+// a bounded wait in the network's tensor-core kernel gave up (synchronous read)
+bool mlbi_net_timed_out(mlb_net *n);
 // force[S][N] = the network's F^hc from the moments' n - n_ref
 cudaError_t mlbi_net_force_from_moments(mlb_net *n, const float4 *mom, float4 *force, cudaStream_t s);
 // sums[0] = sum |fs - fx|^2, sums[1] = sum |fx|^2 over n4 float4 (x, y, z)

@@ -230,6 +230,349 @@ __global__ void __launch_bounds__(128) k_layer3(Geo g, const __nv_bfloat16 *__re
     }
 }
 
+// ------------------------------------------------------------------ layers 2 + 3 on tcgen05 (inference)
+// For lattices with nx a multiple of 128.  A tile is 128 consecutive sites
+// x0 .. x0+127 of one (y, z) row: the 128 rows of the MMA's M dimension and
+// the 128 TMEM lanes.  The 32 -> 32 3^3 convolution is an implicit GEMM
+// D[m][n] = sum_{tap, ci} act1[nbr(m, tap)][ci] W2[tap][n][ci] with
+// K = 27 x 32: per tap two MMAs of M128 N32 K16 (BF16 in, FP32 accumulate in
+// TMEM).  The act1 rows a tile reads, (y+dy, z+dz) for sites x0-1 .. x0+128,
+// sit in shared memory in the K-major layout without swizzle in which every
+// K chunk of 8 channels keeps the sites at a 16-byte stride:
+// [row][chunk][site][8 ch].  A core matrix (8 sites x 16 B) may then start at
+// any site, so the x shift of a tap is only the start address of the A
+// descriptor (LBO = the chunk stride, SBO = 8 sites = 128 B).  W2 is staged
+// once per CTA as B = [tap][chunk][n][8 ch] (LBO 512 B, SBO 128 B).
+//
+// A CTA walks z along (segment, y) columns: its rows form a ring of five z
+// planes (three y rows each).  While the MMAs of tile z (planes z-1 .. z+1)
+// run, plane z+2 is in flight for tile z+1 and plane z+3 is requested for
+// tile z+2, so the copies have two tiles' time to arrive.  The accumulators
+// alternate between two 32-column TMEM buffers: one elected thread issues
+// tile i+1's MMAs before the epilogue of tile i reads its buffer with
+// tcgen05.ld.  The epilogue applies bias, tanh (the hardware approximation,
+// relative error ~2^-11, below the BF16 rounding of the hidden layer) and
+// the 1^3 layer 3 in FP32.  Persistent CTAs, one per SM, 8 warps: warps w
+// and w + 4 read the same 32 TMEM lanes (tcgen05.ld reaches lanes
+// 32 (w mod 4) ..), and each computes the force on one species.
+constexpr int kTcM = 128;
+constexpr int kTcRowSites = kTcM + 2;
+constexpr int kTcLboA = kTcRowSites * 16;                   // bytes between K chunks of a staged row
+constexpr int kTcRowBytes = 4 * kTcLboA;                    // one staged row, 4 chunks of 8 channels
+constexpr int kTcPlaneBytes = 3 * kTcRowBytes;              // rows y-1, y, y+1 of one z plane
+constexpr int kTcRing = 5;                                  // planes z-1 .. z+3 of a tile z
+constexpr int kTcABytes = kTcRing * kTcPlaneBytes;
+constexpr int kTcBBytes = kTaps * 4 * kHid * 16;            // 27 taps x 4 chunks x 32 outputs x 16 B
+constexpr int kTcSmem = kTcBBytes + kTcABytes + 16;         // + mbarrier and the TMEM address
+constexpr int kTcCols = 64;                                 // two accumulators of N = 32 FP32 columns
+// instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHid >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+// spin limit of the mbarrier wait (each try_wait suspends for a while): far
+// above the ~1 us the 54 MMAs of a tile take
+constexpr unsigned kTcSpinLimit = 1u << 20;
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45), fixed 0b001
+    // at 46-48, base offset 0, absolute LBO mode, no swizzle (61-63 = 0)
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase)
+{
+    for (unsigned it = 0; it < kTcSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(phase)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float tanh_fast(float v)
+{
+    float r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ int tc_slot(int zp) { return (zp + kTcRing) % kTcRing; }   // zp >= -1
+
+// cp.async the three rows (y-1, y, y+1) of plane zp (unwrapped, -1 .. nz) of
+// the column (x0, y) into its ring slot, as one commit group
+__device__ __forceinline__ void tc_stage_plane(const Geo &g, const __nv_bfloat16 *__restrict__ act1, uint32_t sA_a,
+                                               int x0, int y, int zp)
+{
+    int zz = zp;
+    zz += zz < 0 ? g.nz : 0; zz -= zz >= g.nz ? g.nz : 0;
+    const uint32_t base = sA_a + (uint32_t)tc_slot(zp) * kTcPlaneBytes;
+    for (int i = threadIdx.x; i < 3 * kTcRowSites * 4; i += blockDim.x) {
+        const int row = i / (kTcRowSites * 4), rem = i % (kTcRowSites * 4), s = rem >> 2, j = rem & 3;
+        int yy = y + row - 1, xx = x0 - 1 + s;
+        yy += yy < 0 ? g.ny : 0; yy -= yy >= g.ny ? g.ny : 0;
+        xx += xx < 0 ? g.nx : 0; xx -= xx >= g.nx ? g.nx : 0;
+        const long long r = xx + (long long)g.nx * (yy + (long long)g.ny * zz);
+        const uint32_t dst = base + row * kTcRowBytes + j * kTcLboA + s * 16;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(act1 + r * kHid + 8 * j) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// the 54 MMAs of tile z into accumulator columns tmem_d, then a commit to
+// the mbarrier.  Descriptors are base descriptors plus compile-time offsets
+// (in 16-byte units of the start-address field; every address stays below
+// 256 KB, so the 14-bit field never carries).
+__device__ __forceinline__ void tc_issue(uint32_t tmem_d, uint32_t sA_a, uint32_t sB_a, int z, uint32_t bar)
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint64_t aplane[3];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+        aplane[dz] = tc_desc(sA_a + (uint32_t)tc_slot(z + dz - 1) * kTcPlaneBytes, kTcLboA, 128);
+    const uint64_t b0 = tc_desc(sB_a, kHid * 16, 128);
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) {
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const int dy = (t / 3) % 3, dx = t % 3;
+            const uint64_t ad = aplane[t / 9] + (uint64_t)((dy * kTcRowBytes + dx * 16 + 2 * kk * kTcLboA) >> 4);
+            const uint64_t bd = b0 + (uint64_t)((t * (4 * kHid * 16) + 2 * kk * (kHid * 16)) >> 4);
+            const uint32_t acc = (t | kk) ? 1u : 0u;
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                         "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc)
+                         : "memory");
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Layer 1 for inference on lattices with nx % 128 == 0: a block computes
+// act1 = tanh(b1 + W1 * x0) for 128 sites x0 .. x0+127 of four rows
+// y0 .. y0+3 of one z plane.  The 18 input rows those read (y0-1 .. y0+4,
+// z-1 .. z+1; sites x0-1 .. x0+128, FP32) are staged in shared memory.  A
+// thread owns 8 channels of 8 sites (m, m+16, .., m+112 of one row), so a
+// tap costs 8 + 4 shared loads for 128 FMAs; the four lanes of a site write
+// its 64 bytes together (a warp stores 8 whole sites).  tanh is the hardware
+// approximation.  Rows past ny (ny % 4 != 0) are computed and not stored.
+constexpr int kL1Rows = 4;
+__global__ void __launch_bounds__(256) k_layer1_rows(Geo g, const float2 *__restrict__ x0,
+                                                     const float *__restrict__ P, __nv_bfloat16 *__restrict__ act1)
+{
+    __shared__ __align__(16) float w[kTaps * kHid * kCin];
+    __shared__ float b[kHid];
+    __shared__ float2 xs[3 * (kL1Rows + 2)][kTcRowSites];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kTaps * kHid * kCin; i += blockDim.x) w[i] = P[kOffW1 + i];
+    for (int i = tid; i < kHid; i += blockDim.x) b[i] = P[kOffB1 + i];
+    const int cg = tid & 3, q = tid >> 2, orow = q >> 4, sl = q & 15;   // channels 8cg.., row y0+orow, sites sl+16k
+    const int nseg = g.nx / kTcM, nyb = (g.ny + kL1Rows - 1) / kL1Rows;
+    const long long ntiles = (long long)nseg * nyb * g.nz;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int seg = (int)(tile % nseg);
+        const long long rest = tile / nseg;
+        const int y0 = (int)(rest % nyb) * kL1Rows, z = (int)(rest / nyb), xb = seg * kTcM;
+        __syncthreads();
+        // staged row (dz + 1) * (kL1Rows + 2) + (yy - y0 + 1)
+        for (int i = tid; i < 3 * (kL1Rows + 2) * kTcRowSites; i += blockDim.x) {
+            const int row = i / kTcRowSites, s = i % kTcRowSites;
+            int yy = y0 + row % (kL1Rows + 2) - 1, zz = z + row / (kL1Rows + 2) - 1, xx = xb - 1 + s;
+            yy = ((yy % g.ny) + g.ny) % g.ny;
+            zz += zz < 0 ? g.nz : 0; zz -= zz >= g.nz ? g.nz : 0;
+            xx += xx < 0 ? g.nx : 0; xx -= xx >= g.nx ? g.nx : 0;
+            xs[row][s] = x0[xx + (long long)g.nx * (yy + (long long)g.ny * zz)];
+        }
+        __syncthreads();
+        float acc[8][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[k][c] = b[8 * cg + c];
+#pragma unroll 1
+        for (int t = 0; t < kTaps; ++t) {
+            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+            const float2 *xr = xs[dz * (kL1Rows + 2) + orow + dy] + sl + dx;
+            const float4 *wt = reinterpret_cast<const float4 *>(w + (t * kHid + 8 * cg) * kCin);
+            float4 ww[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) ww[h] = wt[h];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float2 v = xr[16 * k];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {    // channel 8cg+2h: (ww.x, ww.y); 8cg+2h+1: (ww.z, ww.w)
+                    acc[k][2 * h] = fmaf(v.y, ww[h].y, fmaf(v.x, ww[h].x, acc[k][2 * h]));
+                    acc[k][2 * h + 1] = fmaf(v.y, ww[h].w, fmaf(v.x, ww[h].z, acc[k][2 * h + 1]));
+                }
+            }
+        }
+        const int y = y0 + orow;
+        if (y < g.ny) {
+            const long long rb = xb + sl + (long long)g.nx * (y + (long long)g.ny * z);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint4 pk;
+                pk.x = pack_bf16(tanh_fast(acc[k][0]), tanh_fast(acc[k][1]));
+                pk.y = pack_bf16(tanh_fast(acc[k][2]), tanh_fast(acc[k][3]));
+                pk.z = pack_bf16(tanh_fast(acc[k][4]), tanh_fast(acc[k][5]));
+                pk.w = pack_bf16(tanh_fast(acc[k][6]), tanh_fast(acc[k][7]));
+                *reinterpret_cast<uint4 *>(act1 + (rb + 16 * k) * kHid + 8 * cg) = pk;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_conv23_tc(Geo g, const __nv_bfloat16 *__restrict__ act1,
+                                                      const __nv_bfloat16 *__restrict__ W2f,
+                                                      const float *__restrict__ P, float *__restrict__ out,
+                                                      float4 *__restrict__ force, float inv0, float inv1,
+                                                      int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ float w3[kOut * kHid + kOut], b2[kHid];
+    unsigned char *sB = smem;
+    const uint32_t sB_a = (uint32_t)__cvta_generic_to_shared(sB);
+    const uint32_t sA_a = sB_a + kTcBBytes;
+    const uint32_t bar = sA_a + kTcABytes;
+    const uint32_t slot = bar + 8;
+    const uint32_t *slot_p = reinterpret_cast<const uint32_t *>(smem + kTcBBytes + kTcABytes + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // B chunk (tap, j, n) = W2[tap][n][8j .. 8j+7]
+    for (int i = tid; i < kTaps * 4 * kHid; i += blockDim.x) {
+        const int t = i / (4 * kHid), j = (i / kHid) % 4, n = i % kHid;
+        *reinterpret_cast<uint4 *>(sB + (size_t)i * 16) =
+            *reinterpret_cast<const uint4 *>(W2f + ((size_t)t * kHid + n) * kHid + 8 * j);
+    }
+    for (int i = tid; i < kOut * kHid + kOut; i += blockDim.x) w3[i] = P[kOffW3 + i];
+    for (int i = tid; i < kHid; i += blockDim.x) b2[i] = P[kOffB2 + i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *slot_p;
+
+    // this CTA's tiles: a contiguous range of tile = col * nz + z, col = seg + nseg * y
+    const int nseg = g.nx / kTcM;
+    const long long ntiles = (long long)nseg * g.ny * g.nz;
+    const long long t_begin = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+    if (t_begin < t_end) {
+        uint32_t phase = 0;
+        auto coords = [&](long long t, int &x0, int &y, int &z) {
+            const long long col = t / g.nz;
+            z = (int)(t % g.nz);
+            x0 = (int)(col % nseg) * kTcM;
+            y = (int)(col / nseg);
+        };
+        // tiles a and b (> a) lie in one column: b's planes continue a's ring
+        auto same_col = [&](long long a, long long b) { return b < t_end && a / g.nz == b / g.nz; };
+        {
+            int x0, y, z;
+            coords(t_begin, x0, y, z);
+            for (int dz = -1; dz <= 1; ++dz) tc_stage_plane(g, act1, sA_a, x0, y, z + dz);
+            const bool more = same_col(t_begin, t_begin + 1);
+            if (more) tc_stage_plane(g, act1, sA_a, x0, y, z + 2);
+            if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) tc_issue(tmem, sA_a, sB_a, z, bar);
+        }
+        for (long long tile = t_begin; tile < t_end; ++tile) {
+            int x0, y, z;
+            coords(tile, x0, y, z);
+            const uint32_t buf = (uint32_t)((tile - t_begin) & 1) * 32;
+            const long long n1 = tile + 1;
+            const bool has_n1 = n1 < t_end;
+            // in flight: tile's MMAs (planes z-1 .. z+1) and, within the column, plane z+2
+            bool newer = false;
+            if (same_col(tile, tile + 2)) {
+                tc_stage_plane(g, act1, sA_a, x0, y, z + 3);
+                newer = true;
+            }
+            const bool ok = tc_wait(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                // give up on this call: record it, let the copies and MMAs drain (bounded), free TMEM below
+                if (tid == 0) atomicExch(flag, 1);
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                tc_wait(bar, phase ^ 1u);
+                break;
+            }
+            int nx0 = 0, ny_ = 0, nz_ = 0;
+            if (has_n1) coords(n1, nx0, ny_, nz_);
+            if (has_n1 && !same_col(tile, n1)) {
+                // a new column: nothing is in flight any more, stage its first planes
+                for (int dz = -1; dz <= 1; ++dz) tc_stage_plane(g, act1, sA_a, nx0, ny_, nz_ + dz);
+                newer = same_col(n1, n1 + 1);
+                if (newer) tc_stage_plane(g, act1, sA_a, nx0, ny_, nz_ + 2);
+            }
+            if (newer) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (has_n1 && tid == 0) tc_issue(tmem + (buf ^ 32u), sA_a, sB_a, nz_, bar);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                "[%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(tmem + buf + ((uint32_t)((warp & 3) * 32) << 16)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int sp = warp >> 2;                         // species: outputs 3 sp .. 3 sp + 2
+            const float *w3s = w3 + 3 * sp * kHid;
+            float o[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) o[k] = w3[kOut * kHid + 3 * sp + k];
+#pragma unroll
+            for (int c = 0; c < kHid; ++c) {
+                const float a = tanh_fast(__uint_as_float(v[c]) + b2[c]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) o[k] = fmaf(a, w3s[k * kHid + c], o[k]);
+            }
+            const long long r = x0 + (warp & 3) * 32 + lane + (long long)g.nx * (y + (long long)g.ny * z);
+            if (out)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) out[r * kOut + 3 * sp + k] = o[k];
+            if (force) {
+                const float inv = sp ? inv1 : inv0;
+                force[sp * g.N + r] = make_float4(o[0] * inv, o[1] * inv, o[2] * inv, 0.f);
+            }
+            // the buffer just read is the next MMAs' target after this barrier
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ training
 // targets in the network's units: t[r][3a + i] = F^a_i(r) out_scale_a
 // t = F out_scale in [N][6]; tnorm += sum t^2 (FP64 block sums)
@@ -472,6 +815,9 @@ struct mlb_net {
     float *out = nullptr, *tgt = nullptr, *dout = nullptr;
     double *dev_scalar = nullptr;                                    // [2] loss, sum of target^2
     double *stage = nullptr;                                         // FP64 host-transfer staging
+    int *flag = nullptr;                                             // a bounded device wait gave up
+    bool tc = false;                                                 // nx % 128 == 0: layers 2 + 3 on tcgen05
+    int sms = 0;
     cudaStream_t stream = nullptr;
     long long adam_t = 0;
     bool weights_dirty = true;
@@ -501,12 +847,29 @@ mlb_status refresh_w2(mlb_net *n)
     return MLB_OK;
 }
 
-// forward from x0 (already staged); training keeps the pre-activations
+// forward from x0 (already staged); training keeps the pre-activations.
+// Inference on lattices with nx % 128 == 0 runs layers 2 and 3 as one
+// tcgen05 kernel (FP32 act2); otherwise, and in training, the mma.sync layer 2
+// and layer 3 run separately (BF16 act2, kept for the backward pass).
 mlb_status net_forward(mlb_net *n, bool keep, float *out, float4 *force)
 {
     mlb_status st = refresh_w2(n);
     if (st != MLB_OK) return st;
     const Geo &g = n->g;
+    if (!keep && n->tc) {
+        NET_CUDA(n, cudaFuncSetAttribute(k_conv23_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+        const long long tiles = (long long)(g.nx / kTcM) * g.ny * g.nz;
+        const long long l1_tiles = (long long)(g.nx / kTcM) * ((g.ny + kL1Rows - 1) / kL1Rows) * g.nz;
+        const long long l1_blocks = (long long)n->sms * 2;
+        k_layer1_rows<<<(unsigned)(l1_tiles < l1_blocks ? l1_tiles : l1_blocks), 256, 0, n->stream>>>(g, n->x0,
+                                                                                                      n->P, n->act1);
+        NET_CUDA(n, cudaGetLastError());
+        const unsigned grid = (unsigned)(tiles < n->sms ? tiles : n->sms);
+        k_conv23_tc<<<grid, 256, kTcSmem, n->stream>>>(g, n->act1, n->W2f, n->P, out, force, 1.f / n->out_scale[0],
+                                                        1.f / n->out_scale[1], n->flag);
+        NET_CUDA(n, cudaGetLastError());
+        return MLB_OK;
+    }
     k_layer1<<<grid_of(g.N, 128), 128, 0, n->stream>>>(g, n->x0, n->P, keep ? n->pre1 : nullptr, n->act1);
     NET_CUDA(n, cudaGetLastError());
     NET_CUDA(n, cudaFuncSetAttribute(k_conv32_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem));
@@ -586,6 +949,13 @@ cudaError_t mlbi_force_error(long long n4, const float4 *fs, const float4 *fx, d
     return cudaGetLastError();
 }
 
+bool mlbi_net_timed_out(mlb_net *n)
+{
+    int f = 0;
+    if (cudaMemcpy(&f, n->flag, sizeof f, cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+    return f != 0;
+}
+
 bool mlbi_net_matches(const mlb_net *n, int nx, int ny, int nz)
 {
     return n && n->g.nx == nx && n->g.ny == ny && n->g.nz == nz;
@@ -626,6 +996,12 @@ mlb_status mlb_net_create(const int32_t *dims, mlb_net **out)
     al((void **)&n->dout, sizeof(float) * kOut * N);
     al((void **)&n->dev_scalar, sizeof(double) * 2);
     al((void **)&n->stage, sizeof(double) * 6 * N);
+    al((void **)&n->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->flag, 0, sizeof(int), n->stream);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
+    n->tc = n->g.nx % kTcM == 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, sizeof(float) * kParams, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, sizeof(float) * kParams, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->P, 0, sizeof(float) * kParams, n->stream);
@@ -684,6 +1060,10 @@ mlb_status mlb_net_forward(mlb_net *n, const double *dn, double *force)
     std::vector<float> o((size_t)kOut * N);
     NET_CUDA(n, cudaMemcpyAsync(o.data(), n->out, sizeof(float) * kOut * N, cudaMemcpyDeviceToHost, n->stream));
     NET_CUDA(n, cudaStreamSynchronize(n->stream));
+    if (mlbi_net_timed_out(n)) {
+        n->err = "a bounded wait on the tensor-core MMAs gave up";
+        return MLB_ETIMEOUT;
+    }
     for (long long r = 0; r < N; ++r)
         for (int a = 0; a < 2; ++a)
             for (int i = 0; i < 3; ++i) force[(a * 3 + i) * N + r] = o[r * kOut + 3 * a + i] / n->out_scale[a];
@@ -738,7 +1118,7 @@ void mlb_net_destroy(mlb_net *n)
     for (void *p : {(void *)n->P, (void *)n->G, (void *)n->m, (void *)n->v, (void *)n->W2f, (void *)n->W2b,
                     (void *)n->x0, (void *)n->pre1, (void *)n->act1, (void *)n->pre2, (void *)n->act2,
                     (void *)n->dpre2, (void *)n->dpre1, (void *)n->out, (void *)n->tgt, (void *)n->dout,
-                    (void *)n->dev_scalar, (void *)n->stage})
+                    (void *)n->dev_scalar, (void *)n->stage, (void *)n->flag})
         if (p) cudaFree(p);
     if (n->stream) cudaStreamDestroy(n->stream);
     delete n;

@@ -200,3 +200,34 @@ def recipe(mlb, shape=(64, 8, 8), count: int = 240, seed: int = 21, epochs: int 
     p = net.params()
     net.close()
     return p, ins, outs, data
+
+
+def time_forward(mlb, shape, reps: int = 3, seed: int = 13) -> float:
+    """Milliseconds per network forward (host input staged, force read back)
+    on a lattice of `shape` with He-type random weights and a random input:
+    the kernels' cost does not depend on the values."""
+    import time
+    net = mlb.Net(shape)
+    net.set_params(initial_params(seed))
+    net.set_scales([100.0, 100.0], [100.0, 100.0])
+    N = shape[0] * shape[1] * shape[2]
+    dn = (W.uniform01(seed, 2 * N).reshape(2, N) - 0.5) * 0.01
+    net.forward(dn)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        net.forward(dn)
+    dt = (time.perf_counter() - t0) / reps
+    net.close()
+    return dt * 1e3
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="time the surrogate network's forward on an n^3 lattice")
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    from . import build as _build
+    _build.build()
+    from . import mlb as _mlb
+    print(f"forward {a.size}^3: {time_forward(_mlb, (a.size,) * 3, a.reps):.3f} ms (host staging included)")

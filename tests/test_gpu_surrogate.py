@@ -63,6 +63,28 @@ def test_forward_and_gradient_match_the_fp64_reference(gpu):
     net.close()
 
 
+@pytest.mark.parametrize("shape", [(128, 6, 4), (256, 3, 5)])
+def test_tensor_core_inference_matches_the_fp64_reference(gpu, shape):
+    """Lattices with nx % 128 == 0 run layers 2 and 3 as one tcgen05 kernel
+    (128-site row tiles, FP32 act2); the tiles' x halos wrap periodically."""
+    net = gpu.Net(shape)
+    p = R.random_params(13).astype(np.float32)
+    net.set_params(p)
+    ins, outs = [80.0, 90.0], [400.0, 300.0]
+    net.set_scales(ins, outs)
+    dn, F = _random_frame(shape, 2)
+    x, _ = R.fields(shape, dn, F, ins, outs)
+    out_ref, _ = R.forward(p.astype(np.float64), x)
+    f_ref = np.stack([out_ref[..., o].reshape(-1) for o in range(6)]).reshape(2, 3, -1)
+    f_ref /= np.array(outs)[:, None, None]
+    f_gpu = net.forward(dn)
+    err = np.linalg.norm(f_gpu - f_ref) / np.linalg.norm(f_ref)
+    worst = np.abs(f_gpu - f_ref).max() / np.abs(f_ref).max()
+    print("tcgen05 forward rel error", err, "worst", worst)
+    assert err < 1e-2 and worst < 3e-2
+    net.close()
+
+
 @pytest.fixture(scope="module")
 def frame_sets(gpu):
     shape = (64, 8, 8)
