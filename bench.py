@@ -269,7 +269,7 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ cpu baseline (oracle)
-def cpu_baseline(size, kind="binary", steps=2):
+def cpu_baseline(size, kind="binary", steps=2, one_thread_size=None):
     import numpy as np
     import oracle
     oracle.build()
@@ -280,8 +280,22 @@ def cpu_baseline(size, kind="binary", steps=2):
     oracle.step(lat, f, steps)
     dt = time.perf_counter() - t0
     value = lat.nspecies * lat.nsites * steps / dt / 1e6
-    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{size}^3 lattice of the same physics, {steps} timed steps after 1 warm step, FP64 C oracle, OpenMP"}
+    out = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{size}^3 lattice of the same physics, {steps} timed steps after 1 warm step, FP64 C oracle, OpenMP"}
+    if one_thread_size:
+        cores = oracle.num_threads()
+        lat1, n1 = workload(one_thread_size, kind)
+        f1 = oracle.init(lat1, n1)
+        oracle.set_num_threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.step(lat1, f1, 1)
+            dt1 = time.perf_counter() - t0
+        finally:
+            oracle.set_num_threads(cores)
+        out["one_thread"] = {"value": lat1.nspecies * lat1.nsites / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                             "sample": f"{one_thread_size}^3 lattice, 1 step"}
+    return out
 
 
 # ------------------------------------------------------------------ the GPU arm
@@ -410,6 +424,11 @@ def run_mlb(args, rank, world, local_rank):
         roof = {"kernel": top, "bound": "tensor", "achieved": kt["achieved_tflops"], "peak": tpk,
                 "peak_kind": "measured (MEASURED_PEAKS.json bf16_tflops, burst)", "unit": "TFLOP/s",
                 "frac": kt["achieved_tflops"] / tpk, "traffic": committed_traffic(top, args.size, args.workload)}
+    try:
+        project_copy = mlb.copy_bandwidth(1 << 31, 20)
+    except Exception:
+        project_copy = None
+    roof["peaks_gbs"] = {"measured_copy": peak, "project_copy_kernel": project_copy, "nominal": 7900.0}
     step_bytes = 184.0 * S * N
     step_roof = {"bytes_per_species_site": 184, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
                  "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak, "peak_gbs": peak}
@@ -433,7 +452,8 @@ def run_mlb(args, rank, world, local_rank):
     if surrogate is not None:
         net.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample if args.workload == "binary" else 48, args.workload)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample if args.workload == "binary" else 48, args.workload,
+                                           one_thread_size=64 if args.workload == "binary" else 24)
     if dist:
         dist.destroy_process_group()
     return out

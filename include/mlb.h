@@ -257,6 +257,15 @@ mlb_status mlb_attach_surrogate(mlb_ctx *ctx, mlb_net *net, int32_t recheck_ever
 mlb_status mlb_surrogate_status(mlb_ctx *ctx, int32_t *active, double *last_error, int64_t *rechecks,
                                 int64_t *rejections);
 
+/* Device-to-device copy bandwidth in GB/s (bytes read + written per second):
+ * a grid-stride float4 copy between two fresh buffers of `bytes` each
+ * (>= 1 MiB; use more than the 129 MB L2), `reps` >= 1 launches timed with
+ * CUDA events after two untimed ones, on the current device.  The memory is
+ * allocated and released inside the call.  Errors: MLB_EINVAL, MLB_ENOMEM,
+ * MLB_ECUDA.  (No counterpart in the paper: the HBM peak the kernels'
+ * roofline fractions are quoted against.) */
+mlb_status mlb_copy_bandwidth(int64_t bytes, int32_t reps, double *gbs);
+
 /* Conservation sums without any allocation (the paper has no counterpart:
  * this serves callers that cannot let the library allocate).  A caller whose
  * device memory is all owned by its own memory manager (a framework pool, a

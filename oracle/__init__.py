@@ -83,6 +83,8 @@ def lib():
         L.orc_init.argtypes = [P, dp, dp, dp]
         L.orc_step.argtypes = [P, dp, dp, ctypes.c_int]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -259,6 +261,11 @@ def collide_local(lat, f, n, j, acc):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 def velocity_fields(lat, n, j):

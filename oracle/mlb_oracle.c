@@ -721,6 +721,17 @@ int orc_step(const orc_params *p, double *f, const double *fext, int nsteps)
     return status;
 }
 
+/* threads the OpenMP loops use from now on (n >= 1); a no-op without OpenMP */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

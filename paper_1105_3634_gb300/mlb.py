@@ -91,6 +91,8 @@ def _load():
     L.mlb_kernel_name.restype = ctypes.c_char_p
     L.mlb_conservation_noalloc.argtypes = [vp, dp, ctypes.c_int32, ctypes.c_int64, vp, vp]
     L.mlb_conservation_noalloc.restype = st
+    L.mlb_copy_bandwidth.argtypes = [ctypes.c_int64, ctypes.c_int32, dp]
+    L.mlb_copy_bandwidth.restype = st
     L.mlb_autotune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     L.mlb_autotune.restype = st
     L.mlb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
@@ -147,6 +149,16 @@ def _dp(a):
         return None
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def copy_bandwidth(nbytes: int = 1 << 31, reps: int = 20) -> float:
+    """GB/s of the library's device-to-device float4 copy over two buffers of
+    nbytes (bytes read + written per second; mlb_copy_bandwidth)."""
+    out = ctypes.c_double()
+    rc = lib.mlb_copy_bandwidth(int(nbytes), int(reps), ctypes.byref(out))
+    if rc != 0:
+        raise MLBError(rc, "mlb_copy_bandwidth failed")
+    return float(out.value)
 
 
 def velocity_set():
