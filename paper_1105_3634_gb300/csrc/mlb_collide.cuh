@@ -1,7 +1,7 @@
-// mlb_collide.cuh -- the moments, collision and push streaming of one site,
-// shared by the stand-alone kernels (mlb_kernels.cu) and the fused pass-2 +
-// collision kernels (mlb_pass2.cu), which must agree bit for bit.  Internal
-// header.
+// mlb_collide.cuh -- the moments, site-local contact values, collision and
+// push streaming of one site, shared by the stand-alone kernels
+// (mlb_kernels.cu) and the fused pass-2 + collision kernels (mlb_pass2.cu),
+// which must agree bit for bit.  Internal header.
 #pragma once
 
 #include "mlb_internal.h"
@@ -53,6 +53,40 @@ __device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &p
 // forcing of Eq. evolution scaled by (1 - omega/2), then push streaming:
 // f(r + c_i) with periodic wrap by selects, or halfway bounce-back at walls.
 // population sources: pops(a, i) = f_i^a at the site
+// g_ab(xi) - g_ab(xi_ref) of the BMCSL contact value
+//   g = 1/o + 3 h xi2 / o^2 + 2 h^2 xi2^2 / o^3,   o = 1 - xi3,
+// expanded exactly in the deviations d2 = xi2 - xi2_ref, d3 = xi3 - xi3_ref
+// so that its FP32 value is accurate relative to the deviation itself.
+__device__ __forceinline__ float bmcsl_dev(float h, float xi2r, float xi3r, float d2, float d3)
+{
+    float orf = 1.f - xi3r;
+    float o = orf - d3;
+    float xi2 = xi2r + d2;
+    float o2 = o * o, or2 = orf * orf;
+    float dA = d3 / (o * orf);
+    float dB = 3.f * h * (d2 / o2 + xi2r * d3 * (orf + o) / (o2 * or2));
+    float dC = 2.f * h * h * (d2 * (xi2 + xi2r) / (o2 * o) + xi2r * xi2r * d3 * (or2 + orf * o + o2) / (o2 * o * or2 * orf));
+    return dA + dB + dC;
+}
+
+// Contact values of a site whose smoothing balls are the site itself:
+// dg_q = g_q(xi) - g_q(xi_ref) from the density deviations dn.  Returns
+// false where xi3 >= 1.
+template <int S>
+__device__ __forceinline__ bool site_contact(const mlbi_params &p, const float (&dn)[S],
+                                             float (&dg)[S * (S + 1) / 2])
+{
+    float d2 = 0.f, d3 = 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a) {
+        d2 += p.xi2_coef[a] * dn[a];
+        d3 += p.xi3_coef[a] * dn[a];
+    }
+#pragma unroll
+    for (int q = 0; q < S * (S + 1) / 2; ++q) dg[q] = bmcsl_dev(p.pair[q].h, p.xi2_ref, p.xi3_ref, d2, d3);
+    return p.xi3_ref + d3 < 1.f;
+}
+
 struct GlobalPops {
     const float *__restrict__ f;         // f + r
     long long N;

@@ -44,22 +44,6 @@ __global__ void __launch_bounds__(kBlock) k_moments(const mlbi_params p, const f
 }
 
 // ------------------------------------------------------------------ contact values
-// g_ab(xi) - g_ab(xi_ref) of the BMCSL contact value
-//   g = 1/o + 3 h xi2 / o^2 + 2 h^2 xi2^2 / o^3,   o = 1 - xi3,
-// expanded exactly in the deviations d2 = xi2 - xi2_ref, d3 = xi3 - xi3_ref
-// so that its FP32 value is accurate relative to the deviation itself.
-__device__ __forceinline__ float bmcsl_dev(float h, float xi2r, float xi3r, float d2, float d3)
-{
-    float orf = 1.f - xi3r;
-    float o = orf - d3;
-    float xi2 = xi2r + d2;
-    float o2 = o * o, or2 = orf * orf;
-    float dA = d3 / (o * orf);
-    float dB = 3.f * h * (d2 / o2 + xi2r * d3 * (orf + o) / (o2 * or2));
-    float dC = 2.f * h * h * (d2 * (xi2 + xi2r) / (o2 * o) + xi2r * xi2r * d3 * (or2 + orf * o + o2) / (o2 * o * or2 * orf));
-    return dA + dB + dC;
-}
-
 __global__ void __launch_bounds__(kBX * kBY) k_gfield(mlbi_params p, const float4 *__restrict__ mom,
                                                       const mlbi_entry *__restrict__ tab, float *__restrict__ dg,
                                                       unsigned int *__restrict__ flags)
@@ -98,18 +82,13 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
     const long long N = p.N;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
-        float dn[S], u[S][3];
+        float dn[S], u[S][3], dgv[NP];
         site_moments<S>(p, GlobalPops{f + r, N}, dn, u);
-        float d2 = 0.f, d3 = 0.f;
 #pragma unroll
-        for (int a = 0; a < S; ++a) {
-            mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
-            d2 += p.xi2_coef[a] * dn[a];
-            d3 += p.xi3_coef[a] * dn[a];
-        }
-        if (!(p.xi3_ref + d3 < 1.f)) atomicOr(flags, MLBI_FLAG_XI3);
+        for (int a = 0; a < S; ++a) mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
+        if (!site_contact<S>(p, dn, dgv)) atomicOr(flags, MLBI_FLAG_XI3);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) dg[q * N + r] = bmcsl_dev(p.pair[q].h, p.xi2_ref, p.xi3_ref, d2, d3);
+        for (int q = 0; q < NP; ++q) dg[q * N + r] = dgv[q];
     }
 }
 
