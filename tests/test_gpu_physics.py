@@ -81,3 +81,38 @@ def test_gpu_mutual_diffusion(gpu, sigma, packing, shape):
     D_gpu, D_lin = fitted_D(gpu, lat, n0, 1e-3, 100, 1100, 50)
     print(f"sigma={sigma} packing={packing}: D_gpu={D_gpu:.6f} D_discrete={D_lin:.6f} Eq.dab={eq_dab(sigma, n0):.6f}")
     assert abs(D_gpu - D_lin) < 1e-3 * D_lin
+
+
+def test_gpu_short_wave_oscillates_like_the_linear_operator(gpu):
+    """Packing 0.05, wavelength 8: the concentration amplitude on the GPU
+    changes sign with the complex eigenvalue pair of L(q) (Sec. IV's
+    oscillatory regime), within the FP32 storage and O(amplitude) terms."""
+    lat = W.Lattice(shape=(8, 4, 4), sigma=[1.0, 1.5], tau=1.0)
+    n0 = W.densities_from_packing(0.05, lat.sigma, [0.5, 0.5])
+    amp = 1e-3
+    q = np.array([2 * math.pi / 8, 0.0, 0.0])
+    x = W.coordinate(lat, 0)
+    cosf = np.cos(q[0] * x)
+    n = np.stack([n0[0] * (1 + amp * cosf), n0[1] * (1 - amp * cosf)])
+    Lm, Dn, _ = LM.operator(lat, n0, q)
+    s = LM.initial_state(lat, n0, 0.5 * n0 * np.array([amp, -amp]), np.zeros((2, 3)))
+    ph = np.exp(-1j * q[0] * x) / lat.nsites
+    sim = gpu.Simulation(lat)
+    sim.set_fields(n)
+    w_gpu, w_lin = [], []
+    for _ in range(30):
+        nn, _ = sim.moments()
+        a = (nn - n0[:, None]) @ ph
+        w_gpu.append((n0[1] * a[0] - n0[0] * a[1]).real)
+        b = Dn @ s
+        w_lin.append((n0[1] * b[0] - n0[0] * b[1]).real)
+        sim.step(1)
+        s = Lm @ s
+    sim.close()
+    w_gpu, w_lin = np.array(w_gpu), np.array(w_lin)
+    scale = abs(w_lin[0])
+    print("worst |w_gpu - w_lin| / w0:", np.abs(w_gpu - w_lin).max() / scale)
+    assert np.abs(w_gpu - w_lin).max() < 5e-3 * scale
+    clear = np.abs(w_lin) > 0.02 * scale
+    assert np.array_equal(np.sign(w_gpu[clear]), np.sign(w_lin[clear]))
+    assert np.count_nonzero(np.diff(np.sign(w_lin)) != 0) >= 3
