@@ -61,6 +61,27 @@ def forward(p, x):
     return out, (x, pre1, a1, pre2, a2)
 
 
+def forward_at(p, x, sites):
+    """The network's output at the listed sites (z, y, x) only: each from
+    its 5^3 periodic patch of x (shape (nz, ny, nx, C)), by valid
+    convolutions of the same taps.  Returns (len(sites), 6)."""
+    P = unpack(p)
+    nz, ny, nx = x.shape[:3]
+    out = []
+    for z, y, xx in sites:
+        patch = x[np.ix_([(z + k) % nz for k in range(-2, 3)], [(y + k) % ny for k in range(-2, 3)],
+                         [(xx + k) % nx for k in range(-2, 3)])]          # (5, 5, 5, C), centre (2, 2, 2)
+        pre1 = np.zeros((3, 3, 3, P["W1"].shape[1])) + P["b1"]
+        for t, (dz, dy, dx) in enumerate(TAPS):
+            pre1 += patch[1 + dz:4 + dz, 1 + dy:4 + dy, 1 + dx:4 + dx] @ P["W1"][t].T
+        a1 = act(pre1)
+        pre2 = P["b2"].copy()
+        for t, (dz, dy, dx) in enumerate(TAPS):
+            pre2 += a1[1 + dz, 1 + dy, 1 + dx] @ P["W2"][t].T
+        out.append(act(pre2) @ P["W3"].T + P["b3"])
+    return np.array(out)
+
+
 def loss_and_grad(p, x, target):
     """Relative squared error sum (out - target)^2 / sum target^2 and its gradient."""
     P = unpack(p)

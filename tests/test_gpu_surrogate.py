@@ -85,6 +85,33 @@ def test_tensor_core_inference_matches_the_fp64_reference(gpu, shape):
     net.close()
 
 
+def test_tensor_core_inference_at_256_cubed_on_sampled_sites(gpu):
+    """The bench's lattice, 256^3 (131072 row tiles of the persistent
+    tcgen05 launch bench.py times): 516 sampled sites, the lattice corners
+    among them, against the FP64 reference evaluated on their 5^3 patches."""
+    shape = (256, 256, 256)
+    N = shape[0] * shape[1] * shape[2]
+    net = gpu.Net(shape)
+    p = R.random_params(21).astype(np.float32)
+    net.set_params(p)
+    ins, outs = [80.0, 90.0], [400.0, 300.0]
+    net.set_scales(ins, outs)
+    dn = (W.uniform01(77, 2 * N).reshape(2, N) - 0.5) * 0.02
+    f_gpu = net.forward(dn)
+    x = np.stack([(dn[a] * ins[a]).astype(np.float32).astype(np.float64).reshape(shape[::-1]) for a in range(2)], -1)
+    r = W.uniform01(78, 3 * 512).reshape(512, 3)
+    sites = [(int(a * shape[2]), int(b * shape[1]), int(c * shape[0])) for a, b, c in r]
+    sites += [(0, 0, 0), (255, 255, 255), (0, 255, 127), (255, 0, 128)]    # every wrap
+    ref = R.forward_at(p.astype(np.float64), x, sites)
+    got = np.stack([f_gpu[a, i, [s_[0] * shape[1] * shape[0] + s_[1] * shape[0] + s_[2] for s_ in sites]] * outs[a]
+                    for a in range(2) for i in range(3)], 1)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    worst = np.abs(got - ref).max() / np.abs(ref).max()
+    print("256^3 tcgen05 sampled rel error", err, "worst", worst)
+    assert err < 1e-2 and worst < 3e-2
+    net.close()
+
+
 @pytest.fixture(scope="module")
 def frame_sets(gpu):
     shape = (64, 8, 8)

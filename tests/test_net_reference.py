@@ -32,3 +32,14 @@ def test_taps_read_the_periodic_neighbour():
     S = R.shifted(X, R.TAPS[t])
     assert S[0, 0, 0, 0] == X[1, 4, 1, 0]
     assert S[3, 2, 5, 0] == X[0, 1, 0, 0]
+
+
+def test_forward_at_sampled_sites_equals_the_whole_field():
+    rng = np.random.default_rng(8)
+    p = R.random_params(9)
+    x = rng.normal(0, 1, (5, 6, 7, 2))
+    full, _ = R.forward(p, x)
+    sites = [(0, 0, 0), (4, 5, 6), (2, 3, 1), (1, 5, 0)]
+    at = R.forward_at(p, x, sites)
+    for k, (z, y, xx) in enumerate(sites):
+        assert np.allclose(at[k], full[z, y, xx], rtol=1e-12, atol=1e-12)
