@@ -120,6 +120,18 @@ mlb_status mlb_set_external_force(mlb_ctx *ctx, const double *fext);
 /* Advance nsteps >= 0 time steps (asynchronous on the context's stream). */
 mlb_status mlb_step(mlb_ctx *ctx, int64_t nsteps);
 
+/* One step that also reports the FP64 conservation sums of the state it
+ * starts from, without stalling: the sums are reduced from the moments the
+ * step computes anyway and copied to sums[S + 3] (mass[S] then mom[3], as in
+ * mlb_conservation) asynchronously on the context's stream.  sums is host
+ * memory owned by the caller that must stay valid until the stream has passed
+ * the step (pinned memory makes the copy truly asynchronous); it is written
+ * when the stream reaches it, so read it after mlb_synchronize or after an
+ * event recorded behind the call.  NaN/Inf in the moments is reported by the
+ * next synchronising call.  Errors: MLB_EINVAL (sums NULL), MLB_ESTATE,
+ * MLB_ECUDA. */
+mlb_status mlb_step_monitored(mlb_ctx *ctx, double *sums);
+
 /* Wait for the context's stream; reports numeric faults found by the steps. */
 mlb_status mlb_synchronize(mlb_ctx *ctx);
 

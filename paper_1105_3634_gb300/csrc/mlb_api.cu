@@ -745,6 +745,25 @@ mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
     return MLB_OK;
 }
 
+mlb_status mlb_step_monitored(mlb_ctx *c, double *sums)
+{
+    MLB_GUARD(c);
+    mlb_status st = require_ready(c);
+    if (st != MLB_OK) return st;
+    if (!sums) return fail(c, MLB_EINVAL, "sums is required");
+    const int S = c->desc.nspecies;
+    st = forces(c);
+    if (st != MLB_OK) return st;
+    // the force pass left the moments of the state this step starts from in mom
+    MLB_CUDA(c, mlbi_launch_conservation(c->p, c->b, c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(sums, c->b.sums, sizeof(double) * (S + 3), cudaMemcpyDeviceToHost, c->stream));
+    st = advance(c);
+    if (st != MLB_OK) return st;
+    c->cur ^= 1;
+    ++c->step;
+    return MLB_OK;
+}
+
 int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;

@@ -91,6 +91,8 @@ def _load():
     L.mlb_kernel_name.restype = ctypes.c_char_p
     L.mlb_conservation_noalloc.argtypes = [vp, dp, ctypes.c_int32, ctypes.c_int64, vp, vp]
     L.mlb_conservation_noalloc.restype = st
+    L.mlb_step_monitored.argtypes = [vp, dp]
+    L.mlb_step_monitored.restype = st
     L.mlb_copy_bandwidth.argtypes = [ctypes.c_int64, ctypes.c_int32, dp]
     L.mlb_copy_bandwidth.restype = st
     L.mlb_autotune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
@@ -278,6 +280,14 @@ class Simulation:
         a = np.empty((self.S, 3, self.N))
         self._check(lib.mlb_get_acceleration(self.ctx, _dp(a)))
         return a
+
+    def step_monitored(self, sums: np.ndarray):
+        """One step; the FP64 conservation sums (mass[S], mom[3]) of the state
+        it starts from land in `sums` (float64, S + 3, ideally pinned) when the
+        stream gets there (mlb_step_monitored): read them after synchronize()
+        or a CUDA event recorded behind the call."""
+        assert sums.dtype == np.float64 and sums.flags.c_contiguous and sums.size >= self.S + 3
+        self._check(lib.mlb_step_monitored(self.ctx, _dp(sums)))
 
     def conservation(self):
         m = np.empty(self.S)

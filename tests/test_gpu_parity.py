@@ -371,3 +371,28 @@ def test_tiled_kernels_ragged_boxes(gpu, orc, sigma, shape, wall_axis):
     u = W.random_velocities(lat, 0.005, seed=32)
     w = run_pair(gpu, orc, lat, n, u, checkpoints=(0, 1, 25))
     assert ok(w), w
+
+
+def test_monitored_steps_report_the_conservation_sums(gpu):
+    """mlb_step_monitored: the same populations as mlb_step, and per step the
+    FP64 sums mlb_conservation gives for the state the step starts from, bit
+    for bit."""
+    import torch
+    lat, n = W.binary_config1((40, 12, 10))
+    u = W.random_velocities(lat, 0.01, seed=3)
+    a = gpu.Simulation(lat)
+    b = gpu.Simulation(lat)
+    a.set_fields(n, u)
+    b.set_fields(n, u)
+    S = lat.nspecies
+    bufs = [torch.empty(S + 3, dtype=torch.float64, pin_memory=True).numpy() for _ in range(6)]
+    for k in range(6):
+        a.step_monitored(bufs[k])
+    a.synchronize()
+    for k in range(6):
+        m, p = b.conservation()
+        assert np.array_equal(bufs[k][:S], m) and np.array_equal(bufs[k][S:S + 3], p)
+        b.step(1)
+    assert np.array_equal(a.populations()[0].view(np.uint32), b.populations()[0].view(np.uint32))
+    a.close()
+    b.close()
