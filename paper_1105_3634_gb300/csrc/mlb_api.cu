@@ -394,14 +394,15 @@ struct Timed {
     }
 };
 
-// The force passes of one step on the current populations.
-mlb_status forces(mlb_ctx *c)
+// The force passes of one step on the current populations; sums: the moment
+// pass also leaves the FP64 conservation sums of the state in b.sums.
+mlb_status forces(mlb_ctx *c, bool sums = false)
 {
     if (c->p.local_g) {
         Timed t(c, K_MOMENTS);
-        MLB_CUDA(c, mlbi_launch_moments_g(c->p, c->b, c->cur, c->stream));
+        MLB_CUDA(c, mlbi_launch_moments_g(c->p, c->b, c->cur, c->stream, sums));
     } else {
-        { Timed t(c, K_MOMENTS); MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream)); }
+        { Timed t(c, K_MOMENTS); MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream, sums)); }
         { Timed t(c, K_GFIELD); MLB_CUDA(c, mlbi_launch_gfield(c->p, c->b, c->stream)); }
     }
     if (c->p.attr_r) {
@@ -752,10 +753,8 @@ mlb_status mlb_step_monitored(mlb_ctx *c, double *sums)
     if (st != MLB_OK) return st;
     if (!sums) return fail(c, MLB_EINVAL, "sums is required");
     const int S = c->desc.nspecies;
-    st = forces(c);
+    st = forces(c, true);                          // the moment pass also sums the state
     if (st != MLB_OK) return st;
-    // the force pass left the moments of the state this step starts from in mom
-    MLB_CUDA(c, mlbi_launch_conservation(c->p, c->b, c->stream));
     MLB_CUDA(c, cudaMemcpyAsync(sums, c->b.sums, sizeof(double) * (S + 3), cudaMemcpyDeviceToHost, c->stream));
     st = advance(c);
     if (st != MLB_OK) return st;
@@ -850,8 +849,7 @@ mlb_status mlb_conservation(mlb_ctx *c, double *mass, double *mom)
     if (st != MLB_OK) return st;
     const int S = c->desc.nspecies;
     double h[MLBI_MAXS + 3];
-    MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream));
-    MLB_CUDA(c, mlbi_launch_conservation(c->p, c->b, c->stream));
+    MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream, true));
     MLB_CUDA(c, cudaMemcpyAsync(h, c->b.sums, sizeof(double) * (S + 3), cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     st = check_flags(c);

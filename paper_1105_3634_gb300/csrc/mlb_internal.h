@@ -115,11 +115,15 @@ struct mlbi_buffers {
 #define MLBI_FLAG_NAN 2u
 
 // kernel launchers (one per kernel unit); each returns cudaGetLastError()
-cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
+// sums: also the FP64 conservation sums of the state into b.sums (mass[S],
+// mom[3]; a grid of MLBI_RED_BLOCKS blocks and the final reduction)
+cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s,
+                                bool sums = false);
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
-cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
+cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s,
+                                  bool sums = false);
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s);
 cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 // pass 2 fused with the collision and streaming of f[cur] -> f[cur ^ 1] (no acceleration
@@ -133,7 +137,6 @@ cudaError_t mlbi_launch_export_moments(const mlbi_params &p, const mlbi_buffers 
                                        double *u_out, cudaStream_t s);
 cudaError_t mlbi_launch_import_fext(const mlbi_params &p, const mlbi_buffers &b, const double *fext,
                                     cudaStream_t s);
-cudaError_t mlbi_launch_conservation(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 // float4 [S][N] (x, y, z) -> FP64 [S][3][N]
 cudaError_t mlbi_launch_export_vec(const mlbi_params &p, const float4 *src, double *dst, cudaStream_t s);
 

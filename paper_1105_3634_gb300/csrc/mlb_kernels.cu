@@ -29,18 +29,79 @@
 #include <math.h>
 
 namespace {
+// FP64 global sums of the state, taken while the moments are computed
+// (SUMS): mass sum_r dn^a (n_ref N is added at the end) and momentum
+// sum_a sum_r n^a u^a.  A thread adds its sites in groups of 8 in FP32 (the
+// products n u and the 8-site partials; at most 8 x 2^-24 of a group's
+// magnitude) and accumulates the groups in FP64, so the FP64 pipe, slow on
+// this part, does an eighth of the additions and none of the products; the
+// block sums go to partial[block][S + 3] for k_conservation_final.
 template <int S>
+struct ConsSums {
+    static constexpr int W = S + 3, G = 8;
+    double acc[W];
+    float part[W];
+    int cnt = 0;
+    bool bad = false;
+    __device__ __forceinline__ ConsSums()
+    {
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0.0, part[k] = 0.f;
+    }
+    __device__ __forceinline__ void add(const mlbi_params &p, const float (&dn)[S], const float (&u)[S][3])
+    {
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            bad |= !isfinite(dn[a]) || !isfinite(u[a][0]) || !isfinite(u[a][1]) || !isfinite(u[a][2]);
+            const float n = p.nref[a] + dn[a];
+            part[a] += dn[a];
+            part[S + 0] += n * u[a][0];
+            part[S + 1] += n * u[a][1];
+            part[S + 2] += n * u[a][2];
+        }
+        if (++cnt == G) flush();
+    }
+    __device__ __forceinline__ void flush()
+    {
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] += (double)part[k], part[k] = 0.f;
+        cnt = 0;
+    }
+    __device__ __forceinline__ void store(double *__restrict__ partial, unsigned int *__restrict__ flags)
+    {
+        flush();
+        if (bad) atomicOr(flags, MLBI_FLAG_NAN);
+        __shared__ double sh[kBlock];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            sh[threadIdx.x] = acc[k];
+            __syncthreads();
+            for (int s = kBlock / 2; s > 0; s >>= 1) {
+                if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) partial[blockIdx.x * W + k] = sh[0];
+            __syncthreads();
+        }
+    }
+};
+
+template <int S, bool SUMS>
 __global__ void __launch_bounds__(kBlock) k_moments(const mlbi_params p, const float *__restrict__ f,
-                                                    float4 *__restrict__ mom)
+                                                    float4 *__restrict__ mom, double *__restrict__ partial,
+                                                    unsigned int *__restrict__ flags)
 {
     const long long N = p.N;
+    ConsSums<S> cs;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
         float dn[S], u[S][3];
         site_moments<S>(p, GlobalPops{f + r, N}, dn, u);
 #pragma unroll
         for (int a = 0; a < S; ++a) mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
+        if constexpr (SUMS) cs.add(p, dn, u);
     }
+    if constexpr (SUMS) cs.store(partial, flags);
 }
 
 // ------------------------------------------------------------------ contact values
@@ -73,13 +134,14 @@ __global__ void __launch_bounds__(kBX * kBY) k_gfield(mlbi_params p, const float
 // ------------------------------------------------------------------ moments with local contact values
 // When every smoothing ball is the single site (kappa sigma < 1), g_ab at r
 // depends on the moments at r only: one pass over f gives both.
-template <int S>
+template <int S, bool SUMS>
 __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const float *__restrict__ f,
                                                       float4 *__restrict__ mom, float *__restrict__ dg,
-                                                      unsigned int *__restrict__ flags)
+                                                      unsigned int *__restrict__ flags, double *__restrict__ partial)
 {
     constexpr int NP = S * (S + 1) / 2;
     const long long N = p.N;
+    ConsSums<S> cs;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
         float dn[S], u[S][3], dgv[NP];
@@ -89,7 +151,9 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
         if (!site_contact<S>(p, dn, dgv)) atomicOr(flags, MLBI_FLAG_XI3);
 #pragma unroll
         for (int q = 0; q < NP; ++q) dg[q * N + r] = dgv[q];
+        if constexpr (SUMS) cs.add(p, dn, u);
     }
+    if constexpr (SUMS) cs.store(partial, flags);
 }
 
 template <int S>
@@ -182,40 +246,6 @@ __global__ void __launch_bounds__(kBlock) k_import_fext(mlbi_params p, const dou
 // ------------------------------------------------------------------ FP64 conservation sums
 // Block b sums sites r = b*256 + t, strided by the grid, in a fixed order, then
 // a single block adds the block sums in order: the result is deterministic.
-__global__ void __launch_bounds__(kBlock) k_conservation(mlbi_params p, const float4 *__restrict__ mom,
-                                                         double *__restrict__ partial,
-                                                         unsigned int *__restrict__ flags)
-{
-    const int W = p.S + 3;
-    double acc[MLBI_MAXS + 3];
-    for (int k = 0; k < W; ++k) acc[k] = 0.0;
-    bool bad = false;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < p.N;
-         r += (long long)gridDim.x * blockDim.x) {
-        for (int a = 0; a < p.S; ++a) {
-            float4 v = mom[a * p.N + r];
-            bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
-            const double n = (double)p.nref[a] + (double)v.x;
-            acc[a] += (double)v.x;
-            acc[p.S + 0] += n * (double)v.y;
-            acc[p.S + 1] += n * (double)v.z;
-            acc[p.S + 2] += n * (double)v.w;
-        }
-    }
-    if (bad) atomicOr(flags, MLBI_FLAG_NAN);
-    __shared__ double sh[kBlock];
-    for (int k = 0; k < W; ++k) {
-        sh[threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int s = kBlock / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[blockIdx.x * W + k] = sh[0];
-        __syncthreads();
-    }
-}
-
 __global__ void k_conservation_final(mlbi_params p, const double *__restrict__ partial, int nblocks,
                                      double *__restrict__ sums)
 {
@@ -230,15 +260,26 @@ __global__ void k_conservation_final(mlbi_params p, const double *__restrict__ p
 
 }  // namespace
 
-cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
-{
-    switch (p.S) {
-    case 1: k_moments<1><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
-    case 2: k_moments<2><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
-    case 3: k_moments<3><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
-    case 4: k_moments<4><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom); break;
-    default: return cudaErrorInvalidValue;
+#define MLBI_DISPATCH_S(...)                                                                       \
+    switch (p.S) {                                                                                 \
+    case 1: { constexpr int SS = 1; __VA_ARGS__; } break;                                          \
+    case 2: { constexpr int SS = 2; __VA_ARGS__; } break;                                          \
+    case 3: { constexpr int SS = 3; __VA_ARGS__; } break;                                          \
+    case 4: { constexpr int SS = 4; __VA_ARGS__; } break;                                          \
+    default: return cudaErrorInvalidValue;                                                         \
     }
+
+cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s, bool sums)
+{
+    if (sums) {
+        MLBI_DISPATCH_S((k_moments<SS, true><<<MLBI_RED_BLOCKS, kBlock, 0, s>>>(p, b.f[cur], b.mom, b.partial,
+                                                                                b.flags)));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_conservation_final<<<1, 32, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
+        return cudaGetLastError();
+    }
+    MLBI_DISPATCH_S((k_moments<SS, false><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, nullptr, nullptr)));
     return cudaGetLastError();
 }
 
@@ -248,15 +289,6 @@ cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cuda
     k_gfield<<<tiled_grid(p), dim3(kBX, kBY), 0, s>>>(p, b.mom, b.table, b.dg, b.flags);
     return cudaGetLastError();
 }
-
-#define MLBI_DISPATCH_S(...)                                                                       \
-    switch (p.S) {                                                                                 \
-    case 1: { constexpr int SS = 1; __VA_ARGS__; } break;                                          \
-    case 2: { constexpr int SS = 2; __VA_ARGS__; } break;                                          \
-    case 3: { constexpr int SS = 3; __VA_ARGS__; } break;                                          \
-    case 4: { constexpr int SS = 4; __VA_ARGS__; } break;                                          \
-    default: return cudaErrorInvalidValue;                                                         \
-    }
 
 namespace {
 __global__ void __launch_bounds__(kBlock) k_export_vec(mlbi_params p, const float4 *__restrict__ src,
@@ -279,9 +311,18 @@ cudaError_t mlbi_launch_export_vec(const mlbi_params &p, const float4 *src, doub
     return cudaGetLastError();
 }
 
-cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s, bool sums)
 {
-    MLBI_DISPATCH_S((k_moments_g<SS><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags)));
+    if (sums) {
+        MLBI_DISPATCH_S((k_moments_g<SS, true><<<MLBI_RED_BLOCKS, kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags,
+                                                                                  b.partial)));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_conservation_final<<<1, 32, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
+        return cudaGetLastError();
+    }
+    MLBI_DISPATCH_S((k_moments_g<SS, false><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags,
+                                                                             nullptr)));
     return cudaGetLastError();
 }
 
@@ -313,11 +354,3 @@ cudaError_t mlbi_launch_import_fext(const mlbi_params &p, const mlbi_buffers &b,
     return cudaGetLastError();
 }
 
-cudaError_t mlbi_launch_conservation(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
-{
-    k_conservation<<<MLBI_RED_BLOCKS, kBlock, 0, s>>>(p, b.mom, b.partial, b.flags);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_conservation_final<<<1, 32, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
-    return cudaGetLastError();
-}
