@@ -818,6 +818,7 @@ struct mlb_net {
     int *flag = nullptr;                                             // a bounded device wait gave up
     bool tc = false;                                                 // nx % 128 == 0: layers 2 + 3 on tcgen05
     int sms = 0;
+    cudaError_t cuda_err = cudaSuccess;                              // the last CUDA error recorded
     cudaStream_t stream = nullptr;
     long long adam_t = 0;
     bool weights_dirty = true;
@@ -829,6 +830,7 @@ namespace {
 mlb_status net_fail(mlb_net *n, cudaError_t e, const char *what)
 {
     n->err = std::string(what) + ": " + cudaGetErrorString(e);
+    n->cuda_err = e;
     return MLB_ECUDA;
 }
 
@@ -838,10 +840,10 @@ mlb_status net_fail(mlb_net *n, cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return net_fail((net), e_, #call);                                  \
     } while (0)
 
-mlb_status refresh_w2(mlb_net *n)
+mlb_status refresh_w2(mlb_net *n, cudaStream_t st)
 {
     if (!n->weights_dirty) return MLB_OK;
-    k_w2_bf16<<<(kTaps * kHid * kHid + 255) / 256, 256, 0, n->stream>>>(n->P, n->W2f, n->W2b);
+    k_w2_bf16<<<(kTaps * kHid * kHid + 255) / 256, 256, 0, st>>>(n->P, n->W2f, n->W2b);
     NET_CUDA(n, cudaGetLastError());
     n->weights_dirty = false;
     return MLB_OK;
@@ -851,9 +853,9 @@ mlb_status refresh_w2(mlb_net *n)
 // Inference on lattices with nx % 128 == 0 runs layers 2 and 3 as one
 // tcgen05 kernel (FP32 act2); otherwise, and in training, the mma.sync layer 2
 // and layer 3 run separately (BF16 act2, kept for the backward pass).
-mlb_status net_forward(mlb_net *n, bool keep, float *out, float4 *force)
+mlb_status net_forward(mlb_net *n, bool keep, float *out, float4 *force, cudaStream_t cs)
 {
-    mlb_status st = refresh_w2(n);
+    mlb_status st = refresh_w2(n, cs);
     if (st != MLB_OK) return st;
     const Geo &g = n->g;
     if (!keep && n->tc) {
@@ -861,22 +863,22 @@ mlb_status net_forward(mlb_net *n, bool keep, float *out, float4 *force)
         const long long tiles = (long long)(g.nx / kTcM) * g.ny * g.nz;
         const long long l1_tiles = (long long)(g.nx / kTcM) * ((g.ny + kL1Rows - 1) / kL1Rows) * g.nz;
         const long long l1_blocks = (long long)n->sms * 2;
-        k_layer1_rows<<<(unsigned)(l1_tiles < l1_blocks ? l1_tiles : l1_blocks), 256, 0, n->stream>>>(g, n->x0,
+        k_layer1_rows<<<(unsigned)(l1_tiles < l1_blocks ? l1_tiles : l1_blocks), 256, 0, cs>>>(g, n->x0,
                                                                                                       n->P, n->act1);
         NET_CUDA(n, cudaGetLastError());
         const unsigned grid = (unsigned)(tiles < n->sms ? tiles : n->sms);
-        k_conv23_tc<<<grid, 256, kTcSmem, n->stream>>>(g, n->act1, n->W2f, n->P, out, force, 1.f / n->out_scale[0],
+        k_conv23_tc<<<grid, 256, kTcSmem, cs>>>(g, n->act1, n->W2f, n->P, out, force, 1.f / n->out_scale[0],
                                                         1.f / n->out_scale[1], n->flag);
         NET_CUDA(n, cudaGetLastError());
         return MLB_OK;
     }
-    k_layer1<<<grid_of(g.N, 128), 128, 0, n->stream>>>(g, n->x0, n->P, keep ? n->pre1 : nullptr, n->act1);
+    k_layer1<<<grid_of(g.N, 128), 128, 0, cs>>>(g, n->x0, n->P, keep ? n->pre1 : nullptr, n->act1);
     NET_CUDA(n, cudaGetLastError());
     NET_CUDA(n, cudaFuncSetAttribute(k_conv32_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem));
-    k_conv32_mma<true><<<grid_of((g.N + 15) / 16 * 32, 128), 128, kConvSmem, n->stream>>>(
+    k_conv32_mma<true><<<grid_of((g.N + 15) / 16 * 32, 128), 128, kConvSmem, cs>>>(
         g, n->act1, n->W2f, n->P + kOffB2, nullptr, keep ? n->pre2 : nullptr, n->act2);
     NET_CUDA(n, cudaGetLastError());
-    k_layer3<<<grid_of(g.N, 128), 128, 0, n->stream>>>(g, n->act2, n->P, out, force, 1.f / n->out_scale[0],
+    k_layer3<<<grid_of(g.N, 128), 128, 0, cs>>>(g, n->act2, n->P, out, force, 1.f / n->out_scale[0],
                                                         1.f / n->out_scale[1]);
     NET_CUDA(n, cudaGetLastError());
     return MLB_OK;
@@ -932,12 +934,9 @@ mlb_status stage_frame(mlb_net *n, const double *dn, const double *F)
 // ------------------------------------------------------------------ internal entry points for the step
 cudaError_t mlbi_net_force_from_moments(mlb_net *n, const float4 *mom, float4 *force, cudaStream_t s)
 {
-    cudaStream_t keep = n->stream;
-    n->stream = s;
     k_input_from_mom<<<grid_of(n->g.N, 256), 256, 0, s>>>(n->g, mom, n->in_scale[0], n->in_scale[1], n->x0);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && net_forward(n, false, nullptr, force) != MLB_OK) e = cudaErrorLaunchFailure;
-    n->stream = keep;
+    if (e == cudaSuccess && net_forward(n, false, nullptr, force, s) != MLB_OK) e = n->cuda_err;
     return e;
 }
 
@@ -1055,7 +1054,7 @@ mlb_status mlb_net_forward(mlb_net *n, const double *dn, double *force)
     const long long N = n->g.N;
     mlb_status st = stage_frame(n, dn, nullptr);
     if (st != MLB_OK) return st;
-    st = net_forward(n, false, n->out, nullptr);
+    st = net_forward(n, false, n->out, nullptr, n->stream);
     if (st != MLB_OK) return st;
     std::vector<float> o((size_t)kOut * N);
     NET_CUDA(n, cudaMemcpyAsync(o.data(), n->out, sizeof(float) * kOut * N, cudaMemcpyDeviceToHost, n->stream));
@@ -1074,7 +1073,7 @@ mlb_status mlb_net_gradient(mlb_net *n, const double *dn, const double *F, float
 {
     if (!n || !dn || !F) return MLB_EINVAL;
     mlb_status st = stage_frame(n, dn, F);
-    if (st == MLB_OK) st = net_forward(n, true, n->out, nullptr);
+    if (st == MLB_OK) st = net_forward(n, true, n->out, nullptr, n->stream);
     if (st == MLB_OK) st = net_backward(n);
     if (st != MLB_OK) return st;
     if (grad) NET_CUDA(n, cudaMemcpyAsync(grad, n->G, sizeof(float) * kParams, cudaMemcpyDeviceToHost, n->stream));
@@ -1090,7 +1089,7 @@ mlb_status mlb_net_train(mlb_net *n, const double *dn, const double *F, int32_t 
     if (st != MLB_OK) return st;
     const float b1 = 0.9f, b2 = 0.999f;
     for (int it = 0; it < iters; ++it) {
-        st = net_forward(n, true, n->out, nullptr);
+        st = net_forward(n, true, n->out, nullptr, n->stream);
         if (st == MLB_OK) st = net_backward(n);
         if (st != MLB_OK) return st;
         // the biases keep their set values (zero: the network stays odd in its input)
