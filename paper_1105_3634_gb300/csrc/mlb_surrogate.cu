@@ -1000,7 +1000,7 @@ mlb_status mlb_net_create(const int32_t *dims, mlb_net **out)
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
-    n->tc = n->g.nx % kTcM == 0;
+    n->tc = n->g.nx % kTcM == 0 && (long long)n->g.nx * n->g.ny * kHid < (1ll << 31);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, sizeof(float) * kParams, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, sizeof(float) * kParams, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->P, 0, sizeof(float) * kParams, n->stream);
