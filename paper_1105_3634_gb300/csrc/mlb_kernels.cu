@@ -67,22 +67,22 @@ struct ConsSums {
         for (int k = 0; k < W; ++k) acc[k] += (double)part[k], part[k] = 0.f;
         cnt = 0;
     }
+    // one tree over the block for all W sums at once (independent FP64 adds per level)
     __device__ __forceinline__ void store(double *__restrict__ partial, unsigned int *__restrict__ flags)
     {
         flush();
         if (bad) atomicOr(flags, MLBI_FLAG_NAN);
-        __shared__ double sh[kBlock];
+        __shared__ double sh[W][kBlock];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            sh[threadIdx.x] = acc[k];
-            __syncthreads();
-            for (int s = kBlock / 2; s > 0; s >>= 1) {
-                if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) partial[blockIdx.x * W + k] = sh[0];
+        for (int k = 0; k < W; ++k) sh[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        for (int s = kBlock / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s)
+#pragma unroll
+                for (int k = 0; k < W; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
             __syncthreads();
         }
+        if (threadIdx.x < W) partial[blockIdx.x * W + threadIdx.x] = sh[threadIdx.x][0];
     }
 };
 
@@ -246,16 +246,29 @@ __global__ void __launch_bounds__(kBlock) k_import_fext(mlbi_params p, const dou
 // ------------------------------------------------------------------ FP64 conservation sums
 // Block b sums sites r = b*256 + t, strided by the grid, in a fixed order, then
 // a single block adds the block sums in order: the result is deterministic.
-__global__ void k_conservation_final(mlbi_params p, const double *__restrict__ partial, int nblocks,
-                                     double *__restrict__ sums)
+// Sum of the block partials: two per thread, then one tree over 512 threads
+// for all sums at once (FP64 adds are slow on this part: a 1024-long
+// dependent chain costs ~0.25 ms, the tree 10 levels).
+constexpr int kFinalThreads = 512;
+__global__ void __launch_bounds__(kFinalThreads) k_conservation_final(mlbi_params p, const double *__restrict__ partial,
+                                                                     int nblocks, double *__restrict__ sums)
 {
+    constexpr int WMAX = MLBI_MAXS + 3;
     const int W = p.S + 3;
-    if (threadIdx.x < W) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partial[b * W + threadIdx.x];
-        if (threadIdx.x < p.S) s += (double)p.nref[threadIdx.x] * (double)p.N;   // mass = N n_ref + sum dn
-        sums[threadIdx.x] = s;
+    __shared__ double sh[WMAX][kFinalThreads];
+    for (int k = 0; k < W; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[b * W + k];
+        sh[k][threadIdx.x] = v;
     }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < W; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < W)       // mass = N n_ref + sum dn
+        sums[threadIdx.x] = sh[threadIdx.x][0] + (threadIdx.x < p.S ? (double)p.nref[threadIdx.x] * (double)p.N : 0.0);
 }
 
 }  // namespace
@@ -276,7 +289,7 @@ cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int
                                                                                 b.flags)));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_conservation_final<<<1, 32, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
+        k_conservation_final<<<1, kFinalThreads, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
         return cudaGetLastError();
     }
     MLBI_DISPATCH_S((k_moments<SS, false><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, nullptr, nullptr)));
@@ -318,7 +331,7 @@ cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, i
                                                                                   b.partial)));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_conservation_final<<<1, 32, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
+        k_conservation_final<<<1, kFinalThreads, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
         return cudaGetLastError();
     }
     MLBI_DISPATCH_S((k_moments_g<SS, false><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags,
