@@ -82,6 +82,24 @@ def test_bmcsl_one_species_is_carnahan_starling(orc):
             assert abs(g - cs) < 1e-13 * cs
 
 
+@pytest.mark.parametrize("packing,sigma,n_each,g_expected", [
+    (0.2, (1.0, 1.5), 0.087308, (1.6198, 1.6989, 1.8208)),    # the benchmark mixture
+    (0.3, (2.0, 3.0), 0.016370, (2.1832, 2.3515, 2.6148)),    # the attraction workload's
+])
+def test_bmcsl_contact_values_of_the_workload_states(orc, packing, sigma, n_each, g_expected):
+    """Contact values of the two uniform workload states, as evaluated
+    independently from the BMCSL formula (four decimals), and the densities
+    the packing fraction gives at equal mole fractions."""
+    n = W.densities_from_packing(packing, list(sigma), [0.5, 0.5])
+    assert np.allclose(n, n_each, rtol=0, atol=5e-7)
+    xi2 = math.pi / 6 * sum(nv * s ** 2 for nv, s in zip(n, sigma))
+    xi3 = math.pi / 6 * sum(nv * s ** 3 for nv, s in zip(n, sigma))
+    assert abs(xi3 - packing) < 1e-12
+    pairs = [(sigma[0], sigma[0]), (sigma[0], sigma[1]), (sigma[1], sigma[1])]
+    for (sa, sb), g in zip(pairs, g_expected):
+        assert abs(orc.bmcsl(sa, sb, xi2, xi3) - g) < 6e-5
+
+
 def test_bmcsl_point_particle_limit(orc):
     """A point particle (diameter -> 0) inserted into a hard-sphere fluid has
     the exact scaled-particle contact value 1/(1 - xi3)."""
