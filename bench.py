@@ -40,12 +40,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mlb", "reference"], default="mlb")
     ap.add_argument("--size", type=int, default=None, help="cubic lattice extent (default: the workload's)")
-    ap.add_argument("--workload", choices=["binary", "attraction", "ensemble", "surrogate"], default="binary",
+    ap.add_argument("--workload", choices=["binary", "attraction", "ensemble", "surrogate", "taylor"], default="binary",
                     help="binary: sigma 1/1.5 packing 0.2 (256^3); attraction: sigma 2/3, eps kT/2 tails, "
                          "packing 0.3, 1%% noise (128^3); ensemble: 64 independent binary systems of "
                          "32^3..128^3, packing 0.05-0.20, shear 0-0.05, stepped as one captured graph; "
                          "surrogate: the binary workload with the learned hard-core force (trained first on "
-                         "64x8x8 frames, exact recheck every 50 steps, bound 5%%), timed against the exact step")
+                         "64x8x8 frames, exact recheck every 50 steps, bound 5%%), timed against the exact step; "
+                         "taylor: the 3-species Taylor channel 512x64x64 between moving walls (--size sets the "
+                         "channel's cross-section, the length is 8x)")
     ap.add_argument("--members", type=int, default=64, help="ensemble size")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the default decomposition")
     ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample extent for cpu_baseline")
@@ -54,14 +56,20 @@ def parse_args():
     return ap.parse_args()
 
 
-DEFAULT_SIZE = {"binary": 256, "attraction": 128, "ensemble": 0, "surrogate": 256}
+DEFAULT_SIZE = {"binary": 256, "attraction": 128, "ensemble": 0, "surrogate": 256, "taylor": 64}
 
 
 def workload(size, kind="binary"):
     from paper_1105_3634_gb300 import workloads as W
     if kind == "attraction":
         return W.binary_attraction((size, size, size))
+    if kind == "taylor":
+        return W.taylor_channel((8 * size, size, size))
     return W.binary_config1((size, size, size))
+
+
+def grid_of(size, kind):
+    return [8 * size, size, size] if kind == "taylor" else [size, size, size]
 
 
 def config_dict(size, kind="binary"):
@@ -69,11 +77,17 @@ def config_dict(size, kind="binary"):
             "surrogate": "binary hard spheres sigma=(1,1.5), packing 0.2, tau=1, 5% sine wave, hard-core force "
                          "from the learned surrogate (exact recheck every 50 steps, bound 5%)",
             "attraction": "binary sigma=(2,3), attractive tails -eps(sigma/r)^6 to 2.5 sigma, eps=kT/2, "
-                          "packing 0.3, 1% noise, tau=1"}[kind]
-    return {"workload": f"{desc}, {size}^3 periodic D3Q19",
-            "grid": [size, size, size], "species": 2, "lattice": "D3Q19", "precision": "FP32 populations",
+                          "packing 0.3, 1% noise, tau=1",
+            "taylor": "Taylor channel: solvents sigma=(2,2.5) at packing 0.211, solute sigma=3 at mole fraction "
+                      "1e-3 in a Gaussian pulse of width 8, walls normal to y moving at -/+0.05 along x, tau=1"}[kind]
+    grid = grid_of(size, kind)
+    S = 3 if kind == "taylor" else 2
+    sites = grid[0] * grid[1] * grid[2]
+    where = "channel with bounce-back walls" if kind == "taylor" else "periodic"
+    return {"workload": f"{desc}, {grid[0]}x{grid[1]}x{grid[2]} {where} D3Q19",
+            "grid": grid, "species": S, "lattice": "D3Q19", "precision": "FP32 populations",
             "force_scheme": "semi-implicit half-force shift",
-            "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (2 * 19 * 4 * size ** 3 / 1e9),
+            "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (S * 19 * 4 * sites / 1e9),
             "parallelism": "replicas"}
 
 
@@ -281,7 +295,8 @@ def cpu_baseline(size, kind="binary", steps=2, one_thread_size=None):
     dt = time.perf_counter() - t0
     value = lat.nspecies * lat.nsites * steps / dt / 1e6
     out = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": f"{size}^3 lattice of the same physics, {steps} timed steps after 1 warm step, FP64 C oracle, OpenMP"}
+           "sample": "%s lattice of the same physics, %d timed steps after 1 warm step, FP64 C oracle, OpenMP"
+                     % ("x".join(str(v) for v in grid_of(size, kind)), steps)}
     if one_thread_size:
         cores = oracle.num_threads()
         lat1, n1 = workload(one_thread_size, kind)
@@ -294,7 +309,7 @@ def cpu_baseline(size, kind="binary", steps=2, one_thread_size=None):
         finally:
             oracle.set_num_threads(cores)
         out["one_thread"] = {"value": lat1.nspecies * lat1.nsites / dt1 / 1e6, "unit": UNIT, "cores": 1,
-                             "sample": f"{one_thread_size}^3 lattice, 1 step"}
+                             "sample": "%s lattice, 1 step" % "x".join(str(v) for v in grid_of(one_thread_size, kind))}
     return out
 
 
@@ -463,8 +478,9 @@ def run_mlb(args, rank, world, local_rank):
     if surrogate is not None:
         net.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample if args.workload == "binary" else 48, args.workload,
-                                           one_thread_size=64 if args.workload == "binary" else 24)
+        sample = {"binary": args.cpu_sample, "taylor": 16}.get(args.workload, 48)
+        out["cpu_baseline"] = cpu_baseline(sample, args.workload,
+                                           one_thread_size={"binary": 64, "taylor": 8}.get(args.workload, 24))
     if dist:
         dist.destroy_process_group()
     return out
@@ -603,8 +619,8 @@ def run_reference(args):
         sample_of = "an ensemble member (64^3 sample)"
         config = {"workload": "ensemble of independent binary systems (see the mlb arm)", "members": args.members}
     else:
-        size, kind = min(args.size, 96 if args.workload == "binary" else 40), args.workload
-        sample_of = f"{args.size}^3"
+        size, kind = min(args.size, {"binary": 96, "taylor": 16}.get(args.workload, 40)), args.workload
+        sample_of = "x".join(str(v) for v in grid_of(args.size, args.workload))
         config = config_dict(args.size, args.workload)
     lat, n = workload(size, kind)
     f = oracle.init(lat, n)
@@ -615,7 +631,8 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = lat.nspecies * lat.nsites * args.steps / dt / 1e6
     cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-          "sample": f"{size}^3 lattice of the same physics per step (bounded sample of {sample_of}), FP64 C oracle"}
+          "sample": "%s lattice of the same physics per step (bounded sample of %s), FP64 C oracle"
+                    % ("x".join(str(v) for v in grid_of(size, kind)), sample_of)}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
