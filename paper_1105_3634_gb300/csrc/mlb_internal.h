@@ -84,13 +84,23 @@ __host__ __device__ constexpr long long mlbi_tile_bytes(int S, int R, int ty)
 {
     return (long long)(2 * R + 2) * (32 + 2 * R) * (ty + 2 * R) * (S * 16 + S * (S + 1) / 2 * 4);
 }
-// block height of the tile for (S, R), or 0 when no tile fits (global-memory passes)
+// warps per SM that tiles of block height ty leave resident (the shared-memory
+// bound: 228 KB per SM, 1 KB reserved per block)
+__host__ __device__ constexpr long long mlbi_tile_warps(int S, int R, int ty)
+{
+    return (228 * 1024) / (mlbi_tile_bytes(S, R, ty) + 1024) * ty;
+}
+// block height of the tile for (S, R), or 0 for the global-memory passes: a
+// tile that fits and leaves at least 8 resident warps per SM (one 4-warp
+// block per SM is latency-bound: measured slower than the global passes for
+// three species at reach 3, while one 8-warp block per SM beats them for
+// two species at reach 3)
 __host__ __device__ constexpr int mlbi_tile_ty(int S, int R)
 {
     return R < 1 || R > 3 ? 0
-         : R < 3 ? (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES ? 4 : 0)
+         : R < 3 ? (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES && mlbi_tile_warps(S, R, 4) >= 8 ? 4 : 0)
          : mlbi_tile_bytes(S, R, 8) <= MLBI_MAX_TILE_BYTES ? 8
-         : (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES ? 4 : 0);
+         : (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES && mlbi_tile_warps(S, R, 4) >= 8 ? 4 : 0);
 }
 
 // Device buffers of one context (all carved from one allocation).
