@@ -39,9 +39,8 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    headers = [os.path.join(CSRC, "mlb_internal.h"), os.path.join(CSRC, "mlb_device.cuh"),
-               os.path.join(CSRC, "mlb_passes.cuh"),
-               os.path.join(ROOT, "include", "mlb.h")]
+    headers = [os.path.join(CSRC, h) for h in sorted(os.listdir(CSRC)) if h.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(ROOT, "include", "mlb.h"))
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     os.makedirs(BUILD, exist_ok=True)
     objs = [os.path.join(BUILD, os.path.splitext(s)[0] + ".o") for s in SOURCES]
