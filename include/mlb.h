@@ -128,7 +128,9 @@ mlb_status mlb_step(mlb_ctx *ctx, int64_t nsteps);
  * the step (pinned memory makes the copy truly asynchronous); it is written
  * when the stream reaches it, so read it after mlb_synchronize or after an
  * event recorded behind the call.  NaN/Inf in the moments is reported by the
- * next synchronising call.  Errors: MLB_EINVAL (sums NULL), MLB_ESTATE,
+ * next synchronising call.  The step launches one kernel more than
+ * mlb_launches_per_step says (the final sum); the sums equal mlb_conservation's
+ * on the same state bit for bit.  Errors: MLB_EINVAL (sums NULL), MLB_ESTATE,
  * MLB_ECUDA. */
 mlb_status mlb_step_monitored(mlb_ctx *ctx, double *sums);
 
@@ -147,7 +149,9 @@ mlb_status mlb_get_moments(mlb_ctx *ctx, double *n, double *u);
 mlb_status mlb_get_acceleration(mlb_ctx *ctx, double *acc);
 
 /* FP64 global sums of the current state: mass[a] = sum_r n^a (S doubles),
- * mom[3] = sum_a m^a sum_r j^a.  Returns MLB_ENUMERIC if any moment is NaN/Inf. */
+ * mom[3] = sum_a m^a sum_r j^a (FP64 accumulation of FP32 partial sums over
+ * 8 sites of a thread; any output may be NULL).  Synchronous.  Returns
+ * MLB_ENUMERIC if any moment is NaN/Inf. */
 mlb_status mlb_conservation(mlb_ctx *ctx, double *mass, double *mom);
 
 /* Raw FP32 populations as stored: fdev[a][i][r] = f^a_i(r) - w_i n_ref^a, in the
