@@ -61,3 +61,22 @@ def test_stencil_parameters_reproduce_the_stencil():
     assert np.linalg.norm(got - t) / np.linalg.norm(t) < 1e-4
     P = R.unpack(p)
     assert not P["b1"].any() and not P["b2"].any() and not P["b3"].any()
+
+
+def test_smooth_training_fields():
+    """The training frames' random fields: unit rms, zero mean, the same for
+    the same seed, and a spectrum falling off as exp(-q^2 corr^2 / 2)."""
+    shape = (32, 8, 8)
+    f = SG.smooth_field(shape, 3, 3.0)
+    assert f.shape == (32 * 8 * 8,)
+    assert abs(np.sqrt(np.mean(f * f)) - 1.0) < 1e-12 and abs(f.mean()) < 1e-12
+    assert np.array_equal(f, SG.smooth_field(shape, 3, 3.0))
+    assert not np.array_equal(f, SG.smooth_field(shape, 4, 3.0))
+    # power at the lattice scale against the longest waves, for a long and a short correlation
+    def ratio(corr):
+        p = np.zeros(2)
+        for seed in range(20):
+            F = np.abs(np.fft.fftn(SG.smooth_field(shape, seed, corr).reshape(8, 8, 32))) ** 2
+            p += [F[0, 0, 1:3].sum(), F[4, 4, 12:20].sum()]
+        return p[1] / p[0]
+    assert ratio(3.0) < 1e-6 < ratio(0.5)
