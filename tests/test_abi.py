@@ -84,3 +84,21 @@ def test_null_arguments(mlbmod):
     assert mlbmod.lib.mlb_last_error(None) == b"null context"
     for s in range(7):
         assert mlbmod.lib.mlb_status_string(s)
+
+
+def test_new_entry_points_validate_before_touching_the_gpu(mlbmod):
+    """Host-side argument checks of the surrogate network, the monitored step
+    and the copy-bandwidth probe: refused with MLB_EINVAL, no device call."""
+    L = mlbmod.lib
+    assert L.mlb_net_param_count() == 27 * 32 * 2 + 32 + 27 * 32 * 32 + 32 + 6 * 32 + 6
+    net = ctypes.c_void_p()
+    dims = (ctypes.c_int32 * 3)(2, 8, 8)                  # every extent must be >= 3
+    assert L.mlb_net_create(dims, ctypes.byref(net)) == 1 and not net.value
+    assert L.mlb_net_create(None, ctypes.byref(net)) == 1
+    out = ctypes.c_double(-1.0)
+    assert L.mlb_copy_bandwidth(1 << 19, 5, ctypes.byref(out)) == 1          # below 1 MiB
+    assert L.mlb_copy_bandwidth(1 << 24, 0, ctypes.byref(out)) == 1          # no repetition
+    assert L.mlb_copy_bandwidth(1 << 24, 5, None) == 1
+    sums = np.zeros(8)
+    assert L.mlb_step_monitored(None, sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
+    assert L.mlb_attach_surrogate(None, None, 50, 0.05) == 1
