@@ -70,7 +70,10 @@ def bmcsl_grad(sa, sb, xi2, xi3):
 def operator(lat, n0, q, scheme=None):
     """L(q) as a (19 S) x (19 S) complex matrix, index a*19 + i.
 
-    scheme: 'explicit' or 'semi_implicit' (default: lat.force_scheme).
+    scheme: 'explicit' or 'semi_implicit' (default: lat.force_scheme), or
+    'implicit_coupled': the half-force shift with u* = u + a(u*)/2 solved
+    exactly, every species' u* and the partners' together (the method's
+    semi-implicit scheme takes one Jacobi sweep of it, partners held at u).
     """
     if scheme is None:
         scheme = lat.force_scheme
@@ -147,7 +150,8 @@ def operator(lat, n0, q, scheme=None):
                 Dphi[a] += A[:, None] * Dn[b][None, :]
 
     acc = Dphi / m[:, None, None]
-    if scheme == "semi_implicit":
+    implicit = scheme in ("semi_implicit", "implicit_coupled")
+    if implicit:
         # rest of the field (hard core + attraction) = Dphi minus the velocity part at u
         def vel_part(x):
             out = np.zeros_like(acc)
@@ -166,7 +170,17 @@ def operator(lat, n0, q, scheme=None):
         for a, b, pre, T, T0 in vex:
             Gam[a] += pre * T0[0, 0]
         Frest = Dphi - vel_part(Du)
-        ustar = (Du + (Frest + gain(Du)) / (2 * m[:, None, None])) / (1 + Gam / (2 * m))[:, None, None]
+        if scheme == "implicit_coupled":
+            # (I - V / 2m) u* = u + Frest / 2m with V the velocity part as a 3S x 3S matrix
+            Vm = np.zeros((3 * S, 3 * S), complex)
+            for a, b, pre, T, T0 in vex:
+                Vm[3 * a:3 * a + 3, 3 * b:3 * b + 3] += pre * (T0 if lat.drag_only else T)
+                Vm[3 * a:3 * a + 3, 3 * a:3 * a + 3] -= pre * T0
+            A = np.eye(3 * S) - Vm / (2 * np.repeat(m, 3))[:, None]
+            rhs = (Du + Frest / (2 * m[:, None, None])).reshape(3 * S, dim)
+            ustar = np.linalg.solve(A, rhs).reshape(S, 3, dim)
+        else:
+            ustar = (Du + (Frest + gain(Du)) / (2 * m[:, None, None])) / (1 + Gam / (2 * m))[:, None, None]
         acc = (Frest + vel_part(ustar)) / m[:, None, None]
 
     # collision and streaming
@@ -175,7 +189,7 @@ def operator(lat, n0, q, scheme=None):
         for i in range(Qn):
             row = np.zeros(dim, complex)
             row[a * Qn + i] += 1 - omega
-            if scheme == "semi_implicit":
+            if implicit:
                 ueq = Du[a] + 0.5 * acc[a]
                 row += omega * w[i] * (Dn[a] + n0[a] * (c[i] @ ueq) / CS2)
                 row += (1 - 0.5 * omega) * w[i] * n0[a] * (c[i] @ acc[a]) / CS2
