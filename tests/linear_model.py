@@ -67,13 +67,14 @@ def bmcsl_grad(sa, sb, xi2, xi3):
             1 / o ** 2 + 6 * h * xi2 / o ** 3 + 6 * h * h * xi2 ** 2 / o ** 4)
 
 
-def operator(lat, n0, q, scheme=None):
+def operator(lat, n0, q, scheme=None, sweeps=1):
     """L(q) as a (19 S) x (19 S) complex matrix, index a*19 + i.
 
     scheme: 'explicit' or 'semi_implicit' (default: lat.force_scheme), or
     'implicit_coupled': the half-force shift with u* = u + a(u*)/2 solved
     exactly, every species' u* and the partners' together (the method's
-    semi-implicit scheme takes one Jacobi sweep of it, partners held at u).
+    semi-implicit scheme takes one Jacobi sweep of it, partners held at u;
+    sweeps > 1 repeats the sweep with the partners' u* of the previous one).
     """
     if scheme is None:
         scheme = lat.force_scheme
@@ -180,7 +181,9 @@ def operator(lat, n0, q, scheme=None):
             rhs = (Du + Frest / (2 * m[:, None, None])).reshape(3 * S, dim)
             ustar = np.linalg.solve(A, rhs).reshape(S, 3, dim)
         else:
-            ustar = (Du + (Frest + gain(Du)) / (2 * m[:, None, None])) / (1 + Gam / (2 * m))[:, None, None]
+            ustar = Du
+            for _ in range(sweeps):
+                ustar = (Du + (Frest + gain(ustar)) / (2 * m[:, None, None])) / (1 + Gam / (2 * m))[:, None, None]
         acc = (Frest + vel_part(ustar)) / m[:, None, None]
 
     # collision and streaming
