@@ -48,7 +48,7 @@ class OrcParams(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("nspecies", ctypes.c_int32),
         ("wall_axis", ctypes.c_int32), ("drag_only", ctypes.c_int32),
-        ("explicit_force", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("explicit_force", ctypes.c_int32), ("predictor_sweeps", ctypes.c_int32),
         ("wall_u_lo", ctypes.c_double * 3), ("wall_u_hi", ctypes.c_double * 3),
         ("tau", ctypes.c_double), ("kT", ctypes.c_double), ("kappa", ctypes.c_double),
         ("sigma", ctypes.c_double * MAXS), ("mass", ctypes.c_double * MAXS),
@@ -109,6 +109,7 @@ def params(lat) -> OrcParams:
     if lat.force_scheme not in ("semi_implicit", "explicit"):
         raise ValueError(f"unknown force scheme {lat.force_scheme!r}")
     p.explicit_force = 1 if lat.force_scheme == "explicit" else 0
+    p.predictor_sweeps = int(getattr(lat, "predictor_sweeps", 1))
     for k in range(3):
         p.wall_u_lo[k] = lat.wall_u_lo[k]
         p.wall_u_hi[k] = lat.wall_u_hi[k]

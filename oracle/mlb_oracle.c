@@ -30,7 +30,8 @@
  *   R8' time integration   semi-implicit half-force shift: psi_perp and S are taken at
  *                          u^a + a^a/2, S carries (1 - omega/2), and a is the effective
  *                          field after one Jacobi sweep of u* = u + a(u*)/2 followed by
- *                          the velocity-exchange operator applied to u*; forward Euler
+ *                          the velocity-exchange operator applied to u* (predictor_sweeps > 1:
+ *                          further Jacobi sweeps with the partners' u*); forward Euler
  *                          (a at u, no shift) with the flag explicit_force
  *   R9  collide + stream   f(r+c_i, t+1) = f - omega (f - psi_perp) + S, periodic,
  *                          halfway bounce-back on moving walls
@@ -52,7 +53,7 @@ typedef struct {
     int32_t wall_axis;          /* -1: periodic in all directions; 0,1,2: walls normal to that axis */
     int32_t drag_only;          /* 1: partner velocity taken at r (Eq. gammaab alone) */
     int32_t explicit_force;     /* 1: forward-Euler forcing (R8); 0: semi-implicit half-force shift (R8') */
-    int32_t reserved;
+    int32_t predictor_sweeps;   /* Jacobi sweeps of u* = u + a(u*)/2 (R8'); 0 or 1: one */
     double wall_u_lo[3], wall_u_hi[3];
     double tau, kT, kappa;
     double sigma[ORC_MAXS], mass[ORC_MAXS];
@@ -491,8 +492,10 @@ int orc_accel_sites(const orc_params *p, const double *n, const double *j, const
     velocity_field(p, n, j, vel);
     long M = sites ? nlist : N;
 
-    /* sites where pass 1 is needed: the listed sites and their contact shells */
-    if (!sites) {
+    /* sites where pass 1 is needed: the listed sites and their contact shells
+       (every site when more than one predictor sweep is taken) */
+    const int sweeps = p->predictor_sweeps > 1 ? p->predictor_sweeps : 1;
+    if (!sites || sweeps > 1) {
         memset(need, 1, (size_t)N);
     } else {
         for (long k = 0; k < M; ++k) {
@@ -525,6 +528,24 @@ int orc_accel_sites(const orc_params *p, const double *n, const double *j, const
             solve3(Gam, p->mass[a], b, xs);
             for (int q = 0; q < 3; ++q) ust[((long)a * 3 + q) * N + r] = xs[q];
         }
+    }
+    /* further Jacobi sweeps: the partners' velocities from the previous sweep */
+    if (!p->explicit_force && sweeps > 1) {
+        double *prev = (double *)malloc(sizeof(double) * S * 3 * N);
+        for (int k = 1; k < sweeps; ++k) {
+            memcpy(prev, ust, sizeof(double) * S * 3 * N);
+#pragma omp parallel for schedule(dynamic, 64)
+            for (long r = 0; r < N; ++r)
+                for (int a = 0; a < S; ++a) {
+                    double gain[3], Gam[3][3], b[3], xs[3];
+                    exchange_site(p, &t, n, g, prev, r, a, gain, Gam);
+                    for (int q = 0; q < 3; ++q)
+                        b[q] = vel[((long)a * 3 + q) * N + r] + (rest[((long)a * 3 + q) * N + r] + gain[q]) / (2.0 * p->mass[a]);
+                    solve3(Gam, p->mass[a], b, xs);
+                    for (int q = 0; q < 3; ++q) ust[((long)a * 3 + q) * N + r] = xs[q];
+                }
+        }
+        free(prev);
     }
 
     const double *vfield = p->explicit_force ? vel : ust;

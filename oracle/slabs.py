@@ -44,8 +44,9 @@ CS2 = 1.0 / 3.0
 
 # ------------------------------------------------------------------ geometry
 def halo_depth(lat) -> int:
-    """H = R_s + max(R_s, R_a) + R_b (module docstring), from the oracle's own
-    enumerated stencils."""
+    """H = R_s + max(R_s, R_a) + R_b (module docstring), plus R_s for every
+    further predictor sweep (each reads the partners' u* of the previous one
+    on the shells), from the oracle's own enumerated stencils."""
     S = lat.nspecies
     rs = ra = rb = 0
     for a in range(S):
@@ -60,7 +61,9 @@ def halo_depth(lat) -> int:
                     ra = max(ra, int(np.abs(d).max()))
     for c in range(S):
         rb = max(rb, int(np.floor(lat.kappa * lat.sigma[c] + 1e-12)))
-    return rs + max(rs, ra) + rb
+    sweeps = max(1, int(getattr(lat, "predictor_sweeps", 1)))
+    extra = (sweeps - 1) * rs if lat.force_scheme != "explicit" else 0
+    return rs + max(rs, ra) + rb + extra
 
 
 def slab_bounds(nx: int, P: int) -> List[Tuple[int, int]]:

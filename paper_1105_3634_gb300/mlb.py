@@ -204,6 +204,8 @@ class Simulation:
 
     def __init__(self, lat, stream=None, torch_alloc: bool = True, split_collide: bool = False):
         import torch
+        if getattr(lat, "predictor_sweeps", 1) != 1:
+            raise ValueError("the library's semi-implicit step takes one predictor sweep")
         self.lat = lat
         self.S = lat.nspecies
         self.N = lat.nsites

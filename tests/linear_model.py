@@ -67,7 +67,7 @@ def bmcsl_grad(sa, sb, xi2, xi3):
             1 / o ** 2 + 6 * h * xi2 / o ** 3 + 6 * h * h * xi2 ** 2 / o ** 4)
 
 
-def operator(lat, n0, q, scheme=None, sweeps=1):
+def operator(lat, n0, q, scheme=None, sweeps=None):
     """L(q) as a (19 S) x (19 S) complex matrix, index a*19 + i.
 
     scheme: 'explicit' or 'semi_implicit' (default: lat.force_scheme), or
@@ -78,6 +78,8 @@ def operator(lat, n0, q, scheme=None, sweeps=1):
     """
     if scheme is None:
         scheme = lat.force_scheme
+    if sweeps is None:
+        sweeps = getattr(lat, "predictor_sweeps", 1)
     c, w = d3q19()
     S = lat.nspecies
     Qn = 19

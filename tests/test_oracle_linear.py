@@ -112,3 +112,30 @@ def test_forward_euler_is_unstable_at_config1(orc):
                 L, _, _ = LM.operator(lat, n0, 2 * math.pi * np.array([k, l, m]) / 8)
                 worst = max(worst, np.abs(np.linalg.eigvals(L)).max())
     assert worst < 1 + 1e-9
+
+
+def test_linear_three_predictor_sweeps(orc):
+    """The oracle's predictor with three Jacobi sweeps (the partners' u* of the
+    previous sweep) against L(q) with the same sweeps."""
+    lat = W.Lattice(shape=(16, 3, 2), sigma=[1.0, 1.5], tau=1.0, predictor_sweeps=3)
+    n0 = W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5])
+    q = np.array([2 * math.pi / 16, 2 * math.pi / 3, 0])
+    worst, _ = _run_case(orc, lat, n0, q, [1e-6, -2e-6], np.array([[1e-6, 0, 0], [0, -1e-6, 0]]), [1, 7, 40])
+    assert worst < 1e-7
+
+
+def test_three_sweeps_keep_a_denser_mixture_stable(orc):
+    """Packing 0.3, sigma 1/1.5, 1 % noise: one predictor sweep blows up,
+    three sweeps stay bounded (the linearised step's growth factors)."""
+    def run(sweeps, steps):
+        lat = W.Lattice(shape=(12, 6, 5), sigma=[1.0, 1.5], tau=1.0, predictor_sweeps=sweeps)
+        n0 = W.densities_from_packing(0.3, lat.sigma, [0.5, 0.5])
+        f = orc.init(lat, W.noise(lat, n0, 0.01, seed=17))
+        status = orc.step(lat, f, steps)
+        n, _ = orc.moments(lat, f)
+        ok = status == 0 and np.isfinite(n).all()
+        return ok, (float(np.abs(n - n0[:, None]).max() / n0.max()) if ok else np.inf)
+    ok1, dev1 = run(1, 120)
+    ok3, dev3 = run(3, 300)
+    assert not ok1 or dev1 > 1.0
+    assert ok3 and dev3 < 0.05

@@ -32,6 +32,8 @@ def _case(kind):
     elif kind == "walls_y":
         lat = W.Lattice(shape=(10, 7, 4), sigma=[1.0, 1.25, 1.5], tau=1.2, wall_axis=1,
                         wall_u_lo=(-0.02, 0.0, 0.01), wall_u_hi=(0.03, 0.0, -0.01))
+    elif kind == "three_sweeps":
+        lat = W.Lattice(shape=(16, 6, 5), sigma=[1.0, 1.5], tau=1.0, predictor_sweeps=3)
     elif kind == "explicit_drag":
         lat = W.Lattice(shape=(9, 5, 5), sigma=[1.0, 1.5], tau=0.9, drag_only=True, force_scheme="explicit")
     else:
@@ -58,10 +60,12 @@ def test_halo_depth_of_the_benchmark_physics():
     assert slabs.halo_depth(lat) == 1 + 2
     # sigma = 2 smoothing balls (radius 1) add one plane
     assert slabs.halo_depth(W.Lattice(shape=(8, 8, 8), sigma=[2.0, 3.0])) == 3 + 3 + 1
+    # every further predictor sweep reads one more shell
+    assert slabs.halo_depth(W.Lattice(shape=(8, 8, 8), sigma=[1.0, 1.5], predictor_sweeps=3)) == 2 + 2
 
 
 @pytest.mark.parametrize("kind,P", [("config1", 2), ("config1", 3), ("attraction", 3), ("walls_y", 2),
-                                    ("explicit_drag", 2)])
+                                    ("explicit_drag", 2), ("three_sweeps", 2)])
 def test_slabs_equal_the_monolithic_oracle_bitwise(kind, P):
     lat, f, fext = _case(kind)
     ref = f.copy()
