@@ -499,3 +499,28 @@ def test_couette_profile_between_moving_walls(orc):
     y = np.arange(L)
     expect = -0.02 + 0.05 * (y + 0.5) / L
     assert np.abs(ux - expect).max() < 1e-3 * 0.05
+
+
+@pytest.mark.parametrize("sab", [1.0, 1.5, 2.5, 4.0])
+def test_contact_shell_quadrature_against_the_continuum_sphere(orc, sab):
+    """Reading R3 replaces the contact-sphere integral of Eq. potmeanforce by
+    the lattice shell sum.  For n = a sin(q x): continuum
+    sum over the sphere of s_x n(r + sigma s) = 4 pi a j1(q sigma) cos(q x); lattice
+    (4 pi / |S|) sum_d s_x sin(q (x + d_x)).  Their ratio tends, as q sigma -> 0, to
+    M / sigma with M = (3 / |S|) sum_d |d| s_x^2 (the shell's first moment; Eq.
+    diciotto's gradient term 4 pi sigma / 3 becomes 4 pi M / 3); the deviation at
+    finite q sigma is reported, not asserted."""
+    d = orc.shell(sab).astype(float)
+    r = np.linalg.norm(d, axis=1)
+    s = d / r[:, None]
+    M = 3.0 / len(d) * float(np.sum(r * s[:, 0] ** 2))
+    rows = []
+    for qs in (0.05, 0.5, 1.0, 2.0):
+        q = qs / sab
+        lattice = 4 * math.pi / len(d) * float(np.sum(s[:, 0] * np.sin(q * d[:, 0])))   # coefficient of cos(q x)
+        continuum = 4 * math.pi * (math.sin(qs) / qs ** 2 - math.cos(qs) / qs)          # 4 pi j1(q sigma)
+        rows.append((qs, lattice / continuum))
+    print(f"sigma_ab={sab}: |S|={len(d)}, M/sigma={M / sab:.4f}, lattice/continuum at q sigma = "
+          + ", ".join(f"{qs}: {ratio:.4f}" for qs, ratio in rows))
+    assert abs(rows[0][1] - M / sab) < 1e-3 * M / sab        # the small-q limit is the first moment
+    assert 0.7 < M / sab < 1.3
