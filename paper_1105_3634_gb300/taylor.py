@@ -57,6 +57,31 @@ def passive_scalar_rate(D: float, U: float, kx: float, ky: float, modes: int = 2
     return float(-lam.real / (kx * kx))
 
 
+def passive_scalar_rate_channel(D: float, u_profile, kx: float) -> float:
+    """Slowest decay of c = C(y) e^{i kx x} under dc/dt = -u_x(y) dc/dx + D lap c
+    in a channel of cells y = 0 .. ny-1 (unit spacing) with no-flux walls at
+    -1/2 and ny - 1/2, u_x(y) given per cell: the eigenvalue closest to zero of
+    the finite-volume operator.  Returns D_eff = -rate / kx^2.  For the plane
+    Couette profile u = U (2 (y + 1/2) / h - 1) and kx h -> 0 it tends to the
+    Taylor-Aris value D + U^2 h^2 / (30 D)."""
+    u = np.asarray(u_profile, float)
+    ny = len(u)
+    A = np.diag(-1j * kx * u - D * kx * kx).astype(complex)
+    for i in range(ny - 1):
+        A[i, i + 1] += D
+        A[i + 1, i] += D
+        A[i, i] -= D
+        A[i + 1, i + 1] -= D
+    ev = np.linalg.eigvals(A)
+    return float(-ev[np.argmax(ev.real)].real / (kx * kx))
+
+
+def taylor_aris_couette(D: float, U: float, h: float) -> float:
+    """Plane Couette flow between walls moving at -U and +U, gap h: the
+    long-wave Taylor-Aris coefficient D + U^2 h^2 / (30 D)."""
+    return D + U * U * h * h / (30.0 * D)
+
+
 # ------------------------------------------------------------------ fields
 def cosine_flow(lat: W.Lattice, U: float) -> np.ndarray:
     """u_x(y) = U cos(2 pi y / L_y) = -U cos(2 pi y / L_y + pi) (Eq. ushape), every species."""

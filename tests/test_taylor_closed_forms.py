@@ -61,3 +61,14 @@ def test_eigenvalue_equals_time_integration():
     rate = -np.polyfit(ts, np.log(means), 1)[0]
     expect = T.passive_scalar_rate(D, U, kx, ky)
     assert abs(rate / (kx * kx) - expect) < 1e-5 * expect, (rate / (kx * kx), expect)
+
+
+def test_channel_operator_tends_to_taylor_aris():
+    """The finite-volume channel operator with the plane Couette profile: at
+    small kx h its D_eff is the Taylor-Aris coefficient D + U^2 h^2 / (30 D)."""
+    D, U, h = 0.25, 0.03, 64
+    y = np.arange(h) + 0.5
+    u = U * (2 * y / h - 1)
+    Deff = T.passive_scalar_rate_channel(D, u, 2 * math.pi / (400 * h))
+    assert abs(Deff - T.taylor_aris_couette(D, U, h)) < 2e-3 * Deff
+    assert abs(T.passive_scalar_rate_channel(D, np.zeros(h), 0.1) - D) < 1e-12
