@@ -283,6 +283,28 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ cpu baseline (oracle)
+def host_cpu():
+    """The host's CPU model (lscpu 'Model name', else /proc/cpuinfo) and core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model or "unknown", "nproc": os.cpu_count()}
+
+
 def cpu_baseline(size, kind="binary", steps=2, one_thread_size=None):
     import numpy as np
     import oracle
@@ -294,7 +316,7 @@ def cpu_baseline(size, kind="binary", steps=2, one_thread_size=None):
     oracle.step(lat, f, steps)
     dt = time.perf_counter() - t0
     value = lat.nspecies * lat.nsites * steps / dt / 1e6
-    out = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    out = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "host": host_cpu(),
            "sample": "%s lattice of the same physics, %d timed steps after 1 warm step, FP64 C oracle, OpenMP"
                      % ("x".join(str(v) for v in grid_of(size, kind)), steps)}
     if one_thread_size:
@@ -630,7 +652,7 @@ def run_reference(args):
     oracle.step(lat, f, args.steps)
     dt = time.perf_counter() - t0
     value = lat.nspecies * lat.nsites * args.steps / dt / 1e6
-    cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "host": host_cpu(),
           "sample": "%s lattice of the same physics per step (bounded sample of %s), FP64 C oracle"
                     % ("x".join(str(v) for v in grid_of(size, kind)), sample_of)}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
