@@ -420,7 +420,9 @@ def run_mlb(args, rank, world, local_rank):
         h2d = nh.nbytes / args.steps
         d2h = (S + 3) * 8 + (n_out.nbytes + u_out.nbytes) / args.steps
         e2e = {"value": job_value(world, S, N, args.steps, dt), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.steps,
+               "note": "the one-time set_fields upload and get_moments read-back are spread over the "
+                       "steps: a short run weighs them more",
                "what": "mlb_set_fields from pinned host n, K x mlb_step_monitored (FP64 conservation sums of "
                        "every step to pinned host memory, checked one step behind), mlb_get_moments"}
 

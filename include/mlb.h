@@ -86,9 +86,13 @@ typedef struct {
                                     context creates and owns */
 } mlb_lattice_desc;
 
-/* Create a context: validates desc, allocates every device buffer.  The
- * context then needs mlb_set_species, optionally mlb_set_interactions, and
- * mlb_set_fields (or mlb_set_populations) before mlb_step.
+/* Create a context for one lattice of the method of Sec. II: the D3Q19
+ * populations f^a_i of Eq. (evolution) for nspecies species on an
+ * nx x ny x nz lattice, with relaxation time tau (omega = 1/tau of
+ * Eq. evolution) and k_B T of Eq. (prefactor).  Validates desc, allocates
+ * every device buffer (ownership: the context, through desc->dev_alloc).
+ * The context then needs mlb_set_species, optionally mlb_set_interactions,
+ * and mlb_set_fields (or mlb_set_populations) before mlb_step.
  * Errors: MLB_EINVAL (bad extents, tau <= 1/2, kT != 1/3, wall velocity with a
  * normal component), MLB_ENOMEM, MLB_ECUDA. */
 mlb_status mlb_create(const mlb_lattice_desc *desc, mlb_ctx **out);
@@ -117,48 +121,72 @@ mlb_status mlb_set_fields(mlb_ctx *ctx, const double *n, const double *u);
  * fext: [S][3][N], or NULL to remove it. */
 mlb_status mlb_set_external_force(mlb_ctx *ctx, const double *fext);
 
-/* Advance nsteps >= 0 time steps (asynchronous on the context's stream). */
+/* Advance nsteps >= 0 time steps of Eq. (evolution), Sec. II: per step the
+ * moments (Eq. colonna), the contact values, the effective field
+ * Phi = F^hc + G + F^v of Eqs. (splitforce), (potmeanforce), (gammaab) and
+ * (viscousforce), the collision toward psi_perp of Eq. (prefactor) with the
+ * forcing term, and streaming.  Asynchronous on the context's stream; numeric
+ * faults found on the way are reported by the next synchronising call.
+ * Errors: MLB_EINVAL (nsteps < 0), MLB_ESTATE (no species or state yet, or a
+ * failed context), MLB_ECUDA (a launch failed). */
 mlb_status mlb_step(mlb_ctx *ctx, int64_t nsteps);
 
 /* One step that also reports the FP64 conservation sums of the state it
- * starts from, without stalling: the sums are reduced from the moments the
- * step computes anyway and copied to sums[S + 3] (mass[S] then mom[3], as in
- * mlb_conservation) asynchronously on the context's stream.  sums is host
+ * starts from (Eqs. continuity, momentcomponent), without stalling: the sums
+ * are reduced from the FP32 site moments n^a - n_ref^a and j^a the step
+ * computes anyway (FP32 sums over 8 sites of a thread, accumulated in FP64)
+ * and copied to sums[S + 3] (mass[S] then mom[3], as in mlb_conservation)
+ * asynchronously on the context's stream.  sums is host
  * memory owned by the caller that must stay valid until the stream has passed
  * the step (pinned memory makes the copy truly asynchronous); it is written
  * when the stream reaches it, so read it after mlb_synchronize or after an
  * event recorded behind the call.  NaN/Inf in the moments is reported by the
  * next synchronising call.  The step launches one kernel more than
- * mlb_launches_per_step says (the final sum); the sums equal mlb_conservation's
- * on the same state bit for bit.  Errors: MLB_EINVAL (sums NULL), MLB_ESTATE,
+ * mlb_launches_per_step says (the final sum).  The sums differ from
+ * mlb_conservation's (FP64 sums of the populations themselves) by the FP32
+ * rounding of the site moments and of the 8-site groups: at most
+ * 8 x 2^-24 x sum_r |n^a - n_ref^a| for mass[a] and 8 x 2^-24 x
+ * sum_a sum_r |j^a| for each momentum component.  Errors: MLB_EINVAL (sums NULL), MLB_ESTATE,
  * MLB_ECUDA. */
 mlb_status mlb_step_monitored(mlb_ctx *ctx, double *sums);
 
 /* Wait for the context's stream; reports numeric faults found by the steps. */
 mlb_status mlb_synchronize(mlb_ctx *ctx);
 
-/* Moments of the current populations: n [S][N] and u [S][3][N] (u^a = j^a/n^a,
- * or the barycentric velocity where n^a is below 1e-12).  Either may be NULL. */
+/* Moments of the current populations (Sec. II, Eq. colonna: n^a = sum_i f^a_i,
+ * n^a u^a = sum_i c_i f^a_i): n [S][N] and u [S][3][N] as FP64 host arrays
+ * owned by the caller (u^a = j^a/n^a, or the barycentric velocity of
+ * Eq. massdensity where n^a is below 1e-12).  Either may be NULL.
+ * Synchronous.  Errors: MLB_ESTATE, MLB_ECUDA, MLB_ENUMERIC (NaN/Inf met). */
 mlb_status mlb_get_moments(mlb_ctx *ctx, double *n, double *u);
 
 /* Acceleration a^a = (Phi^a + F^a)/m^a the next step applies to the current
- * state: [S][3][N].  With the half-force shift it is F^hc + G + F^a plus the
+ * state, Phi^a the effective field of Sec. III, Eqs. (splitforce) and
+ * (potmeanforce) with the velocity exchange of Eqs. (gammaab) and
+ * (viscousforce): acc [S][3][N], an FP64 host array owned by the caller.
+ * Synchronous; errors MLB_EINVAL (acc NULL), MLB_ESTATE, MLB_ECUDA.  With the half-force shift it is F^hc + G + F^a plus the
  * velocity-exchange force at u* = u + du, where du solves
  * (I + Gamma/2) du = (F^hc + G + F^a + F^v(u))/2 at each site (one Jacobi
  * sweep of u* = u + a(u*)/2; Gamma = the local friction matrix). */
 mlb_status mlb_get_acceleration(mlb_ctx *ctx, double *acc);
 
-/* FP64 global sums of the current state: mass[a] = sum_r n^a (S doubles),
- * mom[3] = sum_a m^a sum_r j^a (FP64 accumulation of FP32 partial sums over
- * 8 sites of a thread; any output may be NULL).  Synchronous.  Returns
- * MLB_ENUMERIC if any moment is NaN/Inf. */
+/* FP64 global sums of the current state, the quantities the continuity
+ * equations conserve (Sec. II, Eqs. continuity and momentcomponent):
+ * mass[a] = sum_r n^a (S doubles), mom[3] = sum_a m^a sum_r j^a, with
+ * n^a = sum_i f^a_i and j^a = sum_i c_i f^a_i taken from the stored FP32
+ * populations, every population converted to FP64 before it is added
+ * (no FP32 rounding beyond the storage).  Host outputs owned by the caller;
+ * any may be NULL.  Synchronous.  Returns MLB_ENUMERIC if a sum is NaN/Inf. */
 mlb_status mlb_conservation(mlb_ctx *ctx, double *mass, double *mom);
 
-/* Raw FP32 populations as stored: fdev[a][i][r] = f^a_i(r) - w_i n_ref^a, in the
- * velocity order of mlb_velocity_set, plus n_ref [S] and the step counter.
- * Any output pointer may be NULL.  set restores them bit for bit. */
-mlb_status mlb_get_populations(mlb_ctx *ctx, float *fdev, double *nref, int64_t *step);
-mlb_status mlb_set_populations(mlb_ctx *ctx, const float *fdev, const double *nref, int64_t step);
+/* Raw FP32 populations as stored (checkpoint and resume): f_host[a][i][r] =
+ * f^a_i(r) - w_i n_ref^a, a HOST array of S x 19 x N floats owned by the
+ * caller, in the velocity order of mlb_velocity_set, plus n_ref [S] (host)
+ * and the step counter.  Any output pointer may be NULL.  set restores them
+ * bit for bit (f_host and nref required; nref must be FP32-representable).
+ * Synchronous.  Errors: MLB_EINVAL, MLB_ESTATE, MLB_ECUDA. */
+mlb_status mlb_get_populations(mlb_ctx *ctx, float *f_host, double *nref, int64_t *step);
+mlb_status mlb_set_populations(mlb_ctx *ctx, const float *f_host, const double *nref, int64_t step);
 
 /* The D3Q19 velocity set the populations use: c[19][3] and weights w[19]. */
 mlb_status mlb_velocity_set(int32_t *c, double *w);
@@ -290,7 +318,9 @@ mlb_status mlb_copy_bandwidth(int64_t bytes, int32_t reps, double *gbs);
  * mlb_create obtains all of a context's device memory.  This entry point
  * computes the FP64 sums of mlb_conservation from populations the caller
  * holds on the device, and allocates nothing: no cudaMalloc or cudaFree, no
- * allocating library call.  Its reduction keeps its block partial sums in a
+ * allocating library call.  It runs the same two kernels as mlb_conservation
+ * (every population converted to FP64 before it is added), so on the same
+ * populations the two give the same sums bit for bit.  Its reduction keeps its block partial sums in a
  * fixed 28 KiB array (512 blocks x (MLB_MAX_SPECIES + 3) doubles) that every
  * GPU which loads this library holds until the process exits.
  *   fdev    device pointer, [nspecies][19][nsites] FP32 populations minus
@@ -303,8 +333,10 @@ mlb_status mlb_copy_bandwidth(int64_t bytes, int32_t reps, double *gbs);
  * Returns MLB_EINVAL for NULL pointers, nspecies outside 1..MLB_MAX_SPECIES
  * (more species than the fixed array holds), nsites outside 1..2^34 or a
  * non-finite nref; MLB_ECUDA if the lookup or a launch fails (no context, so
- * no message).  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
+ * no message).  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress, a host-side query that allocates
+ * nothing), so a device reset between calls leaves nothing stale; the first
+ * call on a device also loads the library's kernels there, so make that first
  * call before any stream capture.  All calls share the one array, which keeps
  * the last call's contents: every call overwrites each partial it reads, so
  * nothing needs clearing, but calls that overlap on the GPU (other streams,

@@ -849,11 +849,13 @@ mlb_status mlb_conservation(mlb_ctx *c, double *mass, double *mom)
     if (st != MLB_OK) return st;
     const int S = c->desc.nspecies;
     double h[MLBI_MAXS + 3];
-    MLB_CUDA(c, mlbi_launch_moments(c->p, c->b, c->cur, c->stream, true));
+    MLB_CUDA(c, mlbi_launch_pop_sums(c->p, c->b, c->cur, c->stream));
     MLB_CUDA(c, cudaMemcpyAsync(h, c->b.sums, sizeof(double) * (S + 3), cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     st = check_flags(c);
     if (st != MLB_OK) return st;
+    for (int k = 0; k < S + 3; ++k)
+        if (!std::isfinite(h[k])) return fail(c, MLB_ENUMERIC, "non-finite populations met (the state diverged)");
     if (mass)
         for (int a = 0; a < S; ++a) mass[a] = h[a];
     if (mom)
@@ -861,15 +863,15 @@ mlb_status mlb_conservation(mlb_ctx *c, double *mass, double *mom)
     return MLB_OK;
 }
 
-mlb_status mlb_get_populations(mlb_ctx *c, float *fdev, double *nref, int64_t *step)
+mlb_status mlb_get_populations(mlb_ctx *c, float *f_host, double *nref, int64_t *step)
 {
     MLB_GUARD(c);
     mlb_status st = require_ready(c);
     if (st != MLB_OK) return st;
     const int S = c->desc.nspecies;
     const long long N = c->p.N;
-    if (fdev)
-        MLB_CUDA(c, cudaMemcpyAsync(fdev, c->b.f[c->cur], sizeof(float) * S * MLBI_Q * N, cudaMemcpyDeviceToHost,
+    if (f_host)
+        MLB_CUDA(c, cudaMemcpyAsync(f_host, c->b.f[c->cur], sizeof(float) * S * MLBI_Q * N, cudaMemcpyDeviceToHost,
                                     c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     if (nref)
@@ -878,18 +880,18 @@ mlb_status mlb_get_populations(mlb_ctx *c, float *fdev, double *nref, int64_t *s
     return MLB_OK;
 }
 
-mlb_status mlb_set_populations(mlb_ctx *c, const float *fdev, const double *nref, int64_t step)
+mlb_status mlb_set_populations(mlb_ctx *c, const float *f_host, const double *nref, int64_t step)
 {
     MLB_GUARD(c);
     if (!c->species_set) return fail(c, MLB_ESTATE, "call mlb_set_species first");
-    if (!fdev || !nref) return fail(c, MLB_EINVAL, "fdev and nref are required");
+    if (!f_host || !nref) return fail(c, MLB_EINVAL, "f_host and nref are required");
     const int S = c->desc.nspecies;
     const long long N = c->p.N;
     for (int a = 0; a < S; ++a)
         if (!std::isfinite(nref[a]) || nref[a] < 0.0 || (double)(float)nref[a] != nref[a])
             return fail(c, MLB_EINVAL, "nref[%d] must be a non-negative FP32-representable value", a);
     for (long long k = 0; k < (long long)S * MLBI_Q * N; ++k)
-        if (!std::isfinite(fdev[k])) return fail(c, MLB_EINVAL, "population %lld is not finite", k);
+        if (!std::isfinite(f_host[k])) return fail(c, MLB_EINVAL, "population %lld is not finite", k);
     std::vector<double> old = c->nref;
     c->nref.assign(nref, nref + S);
     mlb_status st = rebuild(c);
@@ -897,7 +899,7 @@ mlb_status mlb_set_populations(mlb_ctx *c, const float *fdev, const double *nref
         c->nref = old;
         return st;
     }
-    MLB_CUDA(c, cudaMemcpyAsync(c->b.f[c->cur], fdev, sizeof(float) * S * MLBI_Q * N, cudaMemcpyHostToDevice,
+    MLB_CUDA(c, cudaMemcpyAsync(c->b.f[c->cur], f_host, sizeof(float) * S * MLBI_Q * N, cudaMemcpyHostToDevice,
                                 c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->fields_set = true;

@@ -13,8 +13,10 @@ namespace {
 // dn = sum_i f_i (f stored minus w_i n_ref), j = sum_i c_i f_i taken as the
 // differences of opposite links first, u = j / n (the barycentric velocity
 // where n is tiny), for every species.
+// j: the momentum densities themselves, sum_i c_i f_i
 template <int S, class Pops>
-__device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &pops, float (&dn)[S], float (&u)[S][3])
+__device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &pops, float (&dn)[S], float (&u)[S][3],
+                                             float (&j)[S][3])
 {
     float jx[S], jy[S], jz[S], rho = 0.f, m[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -39,6 +41,7 @@ __device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &p
     const float irho = rho > 0.f ? 1.f / rho : 0.f;
 #pragma unroll
     for (int a = 0; a < S; ++a) {
+        j[a][0] = jx[a]; j[a][1] = jy[a]; j[a][2] = jz[a];
         const float n = p.nref[a] + dn[a];
         const bool ok = n > kTinyDensity;
         const float in = ok ? 1.f / n : 0.f;
@@ -46,6 +49,13 @@ __device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &p
         u[a][1] = ok ? jy[a] * in : m[1] * irho;
         u[a][2] = ok ? jz[a] * in : m[2] * irho;
     }
+}
+
+template <int S, class Pops>
+__device__ __forceinline__ void site_moments(const mlbi_params &p, const Pops &pops, float (&dn)[S], float (&u)[S][3])
+{
+    float j[S][3];
+    site_moments<S>(p, pops, dn, u, j);
 }
 
 // ------------------------------------------------------------------ collide + stream

@@ -129,6 +129,9 @@ struct mlbi_buffers {
 // mom[3]; a grid of MLBI_RED_BLOCKS blocks and the final reduction)
 cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s,
                                 bool sums = false);
+// FP64 sums of the populations f[cur] themselves into b.sums (mass[S], mom[3];
+// mlb_popsum.cuh; b.partial holds the block partials)
+cudaError_t mlbi_launch_pop_sums(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);

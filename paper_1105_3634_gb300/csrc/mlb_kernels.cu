@@ -25,17 +25,22 @@
 #include "mlb_internal.h"
 #include "mlb_device.cuh"
 #include "mlb_collide.cuh"
+#include "mlb_popsum.cuh"
 
 #include <math.h>
 
 namespace {
 // FP64 global sums of the state, taken while the moments are computed
-// (SUMS): mass sum_r dn^a (n_ref N is added at the end) and momentum
-// sum_a sum_r n^a u^a.  A thread adds its sites in groups of 8 in FP32 (the
-// products n u and the 8-site partials; at most 8 x 2^-24 of a group's
-// magnitude) and accumulates the groups in FP64, so the FP64 pipe, slow on
-// this part, does an eighth of the additions and none of the products; the
-// block sums go to partial[block][S + 3] for k_conservation_final.
+// (SUMS, the monitored step): mass sum_r dn^a (n_ref N is added at the end)
+// and momentum sum_a sum_r j^a of the step's own FP32 site moments.  A thread
+// adds its sites in groups of 8 in FP32 and accumulates the groups in FP64,
+// so the FP64 pipe, slow on this part, does an eighth of the additions.  A
+// group's FP32 sum is off by at most 7 x 2^-24 times the sum of its terms'
+// magnitudes, so the total is within 7 x 2^-24 sum_r |dn^a| (mass) and
+// 7 x 2^-24 sum_a sum_r |j^a| (each momentum component) of the FP64 sum of
+// the same site moments.  mlb_conservation sums the populations themselves
+// in FP64 (mlb_popsum.cuh).  The block sums go to partial[block][S + 3] for
+// k_conservation_final.
 template <int S>
 struct ConsSums {
     static constexpr int W = S + 3, G = 8;
@@ -48,16 +53,15 @@ struct ConsSums {
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0.0, part[k] = 0.f;
     }
-    __device__ __forceinline__ void add(const mlbi_params &p, const float (&dn)[S], const float (&u)[S][3])
+    __device__ __forceinline__ void add(const float (&dn)[S], const float (&u)[S][3], const float (&j)[S][3])
     {
 #pragma unroll
         for (int a = 0; a < S; ++a) {
             bad |= !isfinite(dn[a]) || !isfinite(u[a][0]) || !isfinite(u[a][1]) || !isfinite(u[a][2]);
-            const float n = p.nref[a] + dn[a];
             part[a] += dn[a];
-            part[S + 0] += n * u[a][0];
-            part[S + 1] += n * u[a][1];
-            part[S + 2] += n * u[a][2];
+            part[S + 0] += j[a][0];
+            part[S + 1] += j[a][1];
+            part[S + 2] += j[a][2];
         }
         if (++cnt == G) flush();
     }
@@ -95,11 +99,11 @@ __global__ void __launch_bounds__(kBlock) k_moments(const mlbi_params p, const f
     ConsSums<S> cs;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
-        float dn[S], u[S][3];
-        site_moments<S>(p, GlobalPops{f + r, N}, dn, u);
+        float dn[S], u[S][3], j[S][3];
+        site_moments<S>(p, GlobalPops{f + r, N}, dn, u, j);
 #pragma unroll
         for (int a = 0; a < S; ++a) mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
-        if constexpr (SUMS) cs.add(p, dn, u);
+        if constexpr (SUMS) cs.add(dn, u, j);
     }
     if constexpr (SUMS) cs.store(partial, flags);
 }
@@ -144,14 +148,14 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
     ConsSums<S> cs;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
-        float dn[S], u[S][3], dgv[NP];
-        site_moments<S>(p, GlobalPops{f + r, N}, dn, u);
+        float dn[S], u[S][3], j[S][3], dgv[NP];
+        site_moments<S>(p, GlobalPops{f + r, N}, dn, u, j);
 #pragma unroll
         for (int a = 0; a < S; ++a) mom[a * N + r] = make_float4(dn[a], u[a][0], u[a][1], u[a][2]);
         if (!site_contact<S>(p, dn, dgv)) atomicOr(flags, MLBI_FLAG_XI3);
 #pragma unroll
         for (int q = 0; q < NP; ++q) dg[q * N + r] = dgv[q];
-        if constexpr (SUMS) cs.add(p, dn, u);
+        if constexpr (SUMS) cs.add(dn, u, j);
     }
     if constexpr (SUMS) cs.store(partial, flags);
 }
@@ -367,3 +371,10 @@ cudaError_t mlbi_launch_import_fext(const mlbi_params &p, const mlbi_buffers &b,
     return cudaGetLastError();
 }
 
+
+cudaError_t mlbi_launch_pop_sums(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s)
+{
+    mlbps::Nref nr{};
+    for (int a = 0; a < p.S; ++a) nr.v[a] = (double)p.nref[a];
+    return mlbps::launch_pop_sums(b.f[cur], p.S, p.N, nr, b.partial, b.sums, s);
+}
