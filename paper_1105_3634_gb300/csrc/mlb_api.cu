@@ -28,6 +28,7 @@ struct mlb_ctx {
     mlb_lattice_desc desc{};
     mlbi_params p{};
     mlbi_buffers b{};
+    mlbi_maps maps{};
     void *slab = nullptr;
     size_t slab_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -97,6 +98,67 @@ double bmcsl(double sa, double sb, double xi2, double xi3)
 {
     double h = sa * sb / (sa + sb), o = 1.0 - xi3;
     return 1.0 / o + 3.0 * h * xi2 / (o * o) + 2.0 * h * h * xi2 * xi2 / (o * o * o);
+}
+
+// cuTensorMapEncodeTiled from the driver (through the runtime, so that the
+// library links no driver library itself); NULL if unavailable
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    }
+    return fn;
+}
+
+// TMA descriptors of the populations, moments and rest force for the fused
+// pass-2 + collision kernel: boxes of one 32 x 4 tile row block of one z
+// plane, all species (and all 19 populations) at once.  Rows of FP32
+// populations must be 16-byte multiples, so nx % 4 == 0; otherwise (or if the
+// driver lacks the call) maps.ok stays 0 and the kernel stages by cp.async.
+void encode_maps(mlb_ctx *c)
+{
+    mlbi_maps &m = c->maps;
+    m.ok = 0;
+    const mlbi_params &p = c->p;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || p.nx % 4 != 0) return;
+    const cuuint64_t nx = p.nx, ny = p.ny, nz = p.nz, S = p.S;
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    {
+        const cuuint64_t dims[4] = {nx, ny, nz, S * MLBI_Q};
+        const cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+        const cuuint32_t box[4] = {32, 4, 1, (cuuint32_t)(S * MLBI_Q)};
+        for (int k = 0; k < 2; ++k)
+            if (fn(&m.f[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->b.f[k], dims, strides, box, ones,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return;
+    }
+    {
+        const cuuint64_t dims[5] = {4, nx, ny, nz, S};
+        const cuuint64_t strides[4] = {16, nx * 16, nx * ny * 16, nx * ny * nz * 16};
+        const cuuint32_t box[5] = {4, 32, 4, 1, (cuuint32_t)S};
+        if (fn(&m.mom, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, c->b.mom, dims, strides, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+        if (fn(&m.frest, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, c->b.frest, dims, strides, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    }
+    m.ok = 1;
 }
 
 // canonical half of the +-d pairs: first non-zero of (dz, dy, dx) positive
@@ -350,6 +412,7 @@ mlb_status check_flags(mlb_ctx *c)
     unsigned int fl = 0;
     MLB_CUDA(c, cudaMemcpyAsync(&fl, c->b.flags, sizeof fl, cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (fl & MLBI_FLAG_TIMEOUT) return fail(c, MLB_ETIMEOUT, "a bounded wait on a bulk tensor copy gave up");
     if (fl & MLBI_FLAG_NAN) return fail(c, MLB_ENUMERIC, "non-finite moments met (the state diverged)");
     if (fl & MLBI_FLAG_XI3) return fail(c, MLB_ENUMERIC, "packing fraction xi3 >= 1 met at some site");
     return MLB_OK;
@@ -520,7 +583,9 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     }
     if ((bool)d->dev_alloc != (bool)d->dev_free) return bad("dev_alloc and dev_free must be given together");
     const long long N = (long long)d->nx * d->ny * d->nz;
-    if (N > (1ll << 34)) return bad("lattice too large");
+    // site indices are 32-bit on the device (the largest lattice that fits in
+    // memory is well below this)
+    if (N >= (1ll << 31)) return bad("lattice too large: nx * ny * nz must be below 2^31");
     if (d->nz > 65535 || d->ny > 65535 * 4) return bad("ny must be <= 262140 and nz <= 65535");
     if ((long long)d->nx * d->ny >= (1ll << 30)) return bad("nx * ny must be below 2^30");
     const int S = d->nspecies;
@@ -591,6 +656,8 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     c->b.partial = (double *)q; q += sz_part;
     c->b.sums = (double *)q; q += sz_sums;
     c->b.flags = (unsigned int *)q;
+    c->b.maps = &c->maps;
+    encode_maps(c);
     cudaError_t e = cudaMemsetAsync(c->b.flags, 0, sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->b.fext, 0, sz_v4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -3,6 +3,7 @@
 // mlb_attraction.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -103,6 +104,18 @@ __host__ __device__ constexpr int mlbi_tile_ty(int S, int R)
          : (mlbi_tile_bytes(S, R, 4) <= MLBI_MAX_TILE_BYTES && mlbi_tile_warps(S, R, 4) >= 8 ? 4 : 0);
 }
 
+// Bulk tensor (TMA) descriptors of the buffers the fused pass-2 + collision
+// kernel copies plane by plane: the populations f[c] as a 4D FP32 tensor
+// (x, y, z, S*19), the moments and the rest force as 5D (4 components, x,
+// y, z, S).  ok = 0 (no TMA: nx not a multiple of 4, or the encode failed)
+// selects the cp.async variant.
+struct mlbi_maps {
+    CUtensorMap f[2];
+    CUtensorMap mom;
+    CUtensorMap frest;
+    int ok;
+};
+
 // Device buffers of one context (all carved from one allocation).
 struct mlbi_buffers {
     float *f[2];                     // [S][19][N] populations minus w_i n_ref
@@ -118,11 +131,14 @@ struct mlbi_buffers {
     double *partial;                 // [MLBI_RED_BLOCKS][S+3] FP64 block sums
     double *sums;                    // [S+3] final sums
     unsigned int *flags;             // [1] numeric fault flags
+    const mlbi_maps *maps;           // host copy of the TMA descriptors (owned by the context)
 };
 
 #define MLBI_RED_BLOCKS 1024
 #define MLBI_FLAG_XI3 1u
 #define MLBI_FLAG_NAN 2u
+#define MLBI_FLAG_TIMEOUT 4u            // a bounded device wait gave up
+
 
 // kernel launchers (one per kernel unit); each returns cudaGetLastError()
 // sums: also the FP64 conservation sums of the state into b.sums (mass[S],

@@ -25,17 +25,22 @@ __device__ __forceinline__ void solve_sym3(const float G[6], const float b[3], f
     x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
 }
 
+// per species: hf[q] = (F^hc_q, F^v_q), G = friction matrix packed as
+// (xx, yy), (zz, xy), (xz, yz) (see add_pass1), at = attraction
 template <int S>
 struct Acc1 {
-    float hc[S][3], fv[S][3], G[S][6], at[S][3];
+    float2 hf[S][3], G[S][3];
+    float at[S][3];
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
         for (int a = 0; a < S; ++a) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) { hc[a][k] = 0.f; fv[a][k] = 0.f; at[a][k] = 0.f; }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) G[a][k] = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                hf[a][k] = make_float2(0.f, 0.f);
+                G[a][k] = make_float2(0.f, 0.f);
+                at[a][k] = 0.f;
+            }
         }
     }
 };
@@ -79,7 +84,7 @@ __device__ __forceinline__ void pass1_shells(const mlbi_params &p, const Loc &L,
                 float t, sd, wn;
                 pass1_point<DRAG>(P.n, M.n, P.dn - M.dn, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre, w.h[q],
                                   -0.5f * p.pair[q].hc_pre, sdu, t, sd, wn);
-                add_pass1(sx, sy, sz, t, sd, wn, A.hc[a], A.fv[a], A.G[a]);
+                add_pass1(sx, sy, sz, t, sd, wn, A.hf[a], A.G[a]);
             }
         }
     }
@@ -137,13 +142,14 @@ __device__ __forceinline__ void pass1_finish(const mlbi_params &p, long long r, 
 #pragma unroll
     for (int a = 0; a < S; ++a) {
         const float4 fe = p.has_fext ? fext[a * N + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float fr[3] = {A.hc[a][0] + A.at[a][0] + fe.x, A.hc[a][1] + A.at[a][1] + fe.y,
-                             A.hc[a][2] + A.at[a][2] + fe.z};
+        const float fr[3] = {A.hf[a][0].x + A.at[a][0] + fe.x, A.hf[a][1].x + A.at[a][1] + fe.y,
+                             A.hf[a][2].x + A.at[a][2] + fe.z};
         float d[3] = {0.f, 0.f, 0.f};
         if (p.semi_implicit) {
-            const float rhs[3] = {0.5f * (fr[0] + A.fv[a][0]), 0.5f * (fr[1] + A.fv[a][1]),
-                                  0.5f * (fr[2] + A.fv[a][2])};
-            solve_sym3(A.G[a], rhs, d);
+            const float rhs[3] = {0.5f * (fr[0] + A.hf[a][0].y), 0.5f * (fr[1] + A.hf[a][1].y),
+                                  0.5f * (fr[2] + A.hf[a][2].y)};
+            const float G[6] = {A.G[a][0].x, A.G[a][0].y, A.G[a][1].x, A.G[a][1].y, A.G[a][2].x, A.G[a][2].y};
+            solve_sym3(G, rhs, d);
         }
         frest[a * N + r] = make_float4(fr[0], fr[1], fr[2], 0.f);
         pst[a * N + r] = make_float4(c.dn[a], c.u[a][0] + d[0], c.u[a][1] + d[1], c.u[a][2] + d[2]);
@@ -223,7 +229,7 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
                 float t, sd, wn;
                 pass1_point<DRAG>(np, nm, dd, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre, w.h[q],
                                   -0.5f * p.pair[q].hc_pre, sdu, t, sd, wn);
-                add_pass1(sx, sy, sz, HC ? t : 0.f, sd, wn, A.hc[a], A.fv[a], A.G[a]);
+                add_pass1(sx, sy, sz, HC ? t : 0.f, sd, wn, A.hf[a], A.G[a]);
             }
         }
     }
@@ -255,24 +261,36 @@ __device__ __forceinline__ void pass1_cube_class(const mlbi_params &p, const flo
         constexpr int off = cube_kx(k) + T::TXH * cube_ky(k), dz = cube_kz(k);
         const float4 vp = sf[f[1 + dz] + b * T::PLANE + off];
         const float4 vm = sf[f[1 - dz] + b * T::PLANE - off];
-        const float np = nr + vp.x, nm = nr + vm.x, dd = vp.x - vm.x;
-        const float jp = DRAG ? 0.f : cube_dot<k>(il, vp.y, vp.z, vp.w);
-        const float jm = DRAG ? 0.f : cube_dot<k>(il, vm.y, vm.z, vm.w);
+        // the arithmetic of pass1_point with the +d and -d lanes packed
+        const float2 npm = add2(f2(nr, nr), f2(vp.x, vm.x));            // (n(r+d), n(r-d))
+        const float dd = vp.x - vm.x;
+        float2 jpm = f2(0.f, 0.f);                                          // s.u^b(r +- d)
+        if constexpr (!DRAG) {
+            if constexpr (cube_kx(k) != 0) jpm = fma2(f2(cube_kx(k) * il, cube_kx(k) * il), f2(vp.y, vm.y), jpm);
+            if constexpr (cube_ky(k) != 0) jpm = fma2(f2(cube_ky(k) * il, cube_ky(k) * il), f2(vp.z, vm.z), jpm);
+            if constexpr (cube_kz(k) != 0) jpm = fma2(f2(cube_kz(k) * il, cube_kz(k) * il), f2(vp.w, vm.w), jpm);
+        }
 #pragma unroll
         for (int a = 0; a < S; ++a) {
             if (!has[a]) continue;
             const int q = pair_of(a, b, S);
-            const float dgp = sg[g[1 + dz] + q * T::PLANE + off];
-            const float dgm = sg[g[1 - dz] + q * T::PLANE - off];
-            const float sdu = DRAG ? cube_dot<k>(il, c.u[a][0] - c.u[b][0], c.u[a][1] - c.u[b][1],
-                                                 c.u[a][2] - c.u[b][2])
-                                   : 0.f;
-            const float su = DRAG ? 0.f : cube_dot<k>(il, c.u[a][0], c.u[a][1], c.u[a][2]);
-            float t, sd, wn;
-            pass1_point<DRAG>(np, nm, dd, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre, w.h[q],
-                              -0.5f * p.pair[q].hc_pre, sdu, t, sd, wn);
-            if constexpr (HC) cube_add<k>(il, t, A.hc[a]);
-            cube_add<k>(il, sd, A.fv[a]);
+            const float2 dg2 = f2(sg[g[1 + dz] + q * T::PLANE + off], sg[g[1 - dz] + q * T::PLANE - off]);
+            const float k1 = 0.5f * p.pair[q].vx_pre;
+            const float2 gpm = fma2(f2(k1, k1), dg2, f2(w.kp[q], w.kp[q]));   // exchange weights at r +- d
+            const float2 hpm = mul2(gpm, npm);
+            const float wn = hpm.x + hpm.y;
+            float sd;
+            if constexpr (DRAG) {
+                const float sdu = cube_dot<k>(il, c.u[a][0] - c.u[b][0], c.u[a][1] - c.u[b][1], c.u[a][2] - c.u[b][2]);
+                sd = -wn * sdu;
+            } else {
+                const float su = cube_dot<k>(il, c.u[a][0], c.u[a][1], c.u[a][2]);
+                const float2 j2 = add2(jpm, f2(-su, -su));                   // s.(u^b(r +- d) - u^a(r))
+                sd = fmaf(hpm.x, j2.x, hpm.y * j2.y);
+            }
+            const float t = HC ? fmaf(w.h[q], dd, (-0.5f * p.pair[q].hc_pre) * fmaf(npm.x, dg2.x, -npm.y * dg2.y))
+                               : 0.f;
+            cube_add2<k>(il, f2(t, sd), A.hf[a]);
             cube_add_ss<k>(il, wn, A.G[a]);
         }
     });

@@ -39,6 +39,22 @@ __device__ __forceinline__ void store_acc(const mlbi_params &p, long long r, con
     }
 }
 
+template <int S>
+__device__ __forceinline__ void zero_acc(float (&acc)[S][3])
+{
+#pragma unroll
+    for (int a = 0; a < S; ++a) acc[a][0] = acc[a][1] = acc[a][2] = 0.f;
+}
+
+// the rest force F^hc + G + F_ext is added after the shell sums (the same
+// order in every variant, so the fused and split launches agree bit for bit)
+__device__ __forceinline__ void add_rest(float (&acc)[3], const float4 fr)
+{
+    acc[0] = fr.x + acc[0];
+    acc[1] = fr.y + acc[1];
+    acc[2] = fr.z + acc[2];
+}
+
 // a^a = frest^a + vx_ab sum_{+-d} s s.[(g(r)+g(r+d))/2 n^b(r+d) (u*^b(r+d) - u*^a(r))]
 // (drag only: -wn s.(u*^a - u*^b)(r) per point)
 template <int S, bool DRAG, bool INTERIOR>
@@ -102,13 +118,11 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const 
     float us[S][3];
     centre_ustar<S>(p, pst, r, us);
     float acc[S][3];
-#pragma unroll
-    for (int a = 0; a < S; ++a) {
-        const float4 fr = frest[a * N + r];
-        acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
-    }
+    zero_acc<S>(acc);
     if (L.interior) pass2_shells<S, DRAG, true>(p, L, w, us, pst, dg, tab, acc);
     else pass2_shells<S, DRAG, false>(p, L, w, us, pst, dg, tab, acc);
+#pragma unroll
+    for (int a = 0; a < S; ++a) add_rest(acc[a], frest[a * N + r]);
     store_acc<S>(p, r, acc, acc_f, acc_out);
 }
 
@@ -177,20 +191,30 @@ __device__ __forceinline__ void pass2_cube_class(const mlbi_params &p, const flo
         constexpr int off = cube_kx(k) + T::TXH * cube_ky(k), dz = cube_kz(k);
         const float4 vp = sf[f[1 + dz] + b * T::PLANE + off];
         const float4 vm = sf[f[1 - dz] + b * T::PLANE - off];
-        const float np = nr + vp.x, nm = nr + vm.x;
-        const float jp = DRAG ? 0.f : cube_dot<k>(il, vp.y, vp.z, vp.w);
-        const float jm = DRAG ? 0.f : cube_dot<k>(il, vm.y, vm.z, vm.w);
+        // the arithmetic of pass2_point with the +d and -d lanes packed
+        const float2 npm = add2(f2(nr, nr), f2(vp.x, vm.x));
+        float2 jpm = f2(0.f, 0.f);
+        if constexpr (!DRAG) {
+            if constexpr (cube_kx(k) != 0) jpm = fma2(f2(cube_kx(k) * il, cube_kx(k) * il), f2(vp.y, vm.y), jpm);
+            if constexpr (cube_ky(k) != 0) jpm = fma2(f2(cube_ky(k) * il, cube_ky(k) * il), f2(vp.z, vm.z), jpm);
+            if constexpr (cube_kz(k) != 0) jpm = fma2(f2(cube_kz(k) * il, cube_kz(k) * il), f2(vp.w, vm.w), jpm);
+        }
 #pragma unroll
         for (int a = 0; a < S; ++a) {
             if (!has[a]) continue;
             const int q = pair_of(a, b, S);
-            const float dgp = sg[g[1 + dz] + q * T::PLANE + off];
-            const float dgm = sg[g[1 - dz] + q * T::PLANE - off];
-            const float sdu = DRAG ? cube_dot<k>(il, us[a][0] - us[b][0], us[a][1] - us[b][1], us[a][2] - us[b][2])
-                                   : 0.f;
-            const float su = DRAG ? 0.f : cube_dot<k>(il, us[a][0], us[a][1], us[a][2]);
-            const float sd = pass2_point<DRAG>(np, nm, jp - su, jm - su, dgp, dgm, w.kp[q], 0.5f * p.pair[q].vx_pre,
-                                               sdu);
+            const float2 dg2 = f2(sg[g[1 + dz] + q * T::PLANE + off], sg[g[1 - dz] + q * T::PLANE - off]);
+            const float k1 = 0.5f * p.pair[q].vx_pre;
+            const float2 hpm = mul2(fma2(f2(k1, k1), dg2, f2(w.kp[q], w.kp[q])), npm);
+            float sd;
+            if constexpr (DRAG) {
+                const float sdu = cube_dot<k>(il, us[a][0] - us[b][0], us[a][1] - us[b][1], us[a][2] - us[b][2]);
+                sd = -(hpm.x + hpm.y) * sdu;
+            } else {
+                const float su = cube_dot<k>(il, us[a][0], us[a][1], us[a][2]);
+                const float2 j2 = add2(jpm, f2(-su, -su));
+                sd = fmaf(hpm.x, j2.x, hpm.y * j2.y);
+            }
             cube_add<k>(il, sd, acc[a]);
         }
     });
@@ -213,8 +237,8 @@ __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *s
     }
 }
 
-// the acceleration of the site at ring position kz of the tile (centre slot cs)
-// (acc holds the rest force frest on entry)
+// the shell sums of the acceleration of the site at ring position kz of the
+// tile (centre slot cs), added to acc
 template <int S, int R, bool DRAG, int TY>
 __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *__restrict__ tab, const float4 *sf,
                                            const float *sg, int kz, int cidx, float (&acc)[S][3])
@@ -267,12 +291,10 @@ __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S
         if (!active) continue;
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
         float acc[S][3];
-#pragma unroll
-        for (int a = 0; a < S; ++a) {
-            const float4 fr = frest[a * p.N + r];
-            acc[a][0] = fr.x; acc[a][1] = fr.y; acc[a][2] = fr.z;
-        }
+        zero_acc<S>(acc);
         pass2_site<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, acc);
+#pragma unroll
+        for (int a = 0; a < S; ++a) add_rest(acc[a], frest[a * p.N + r]);
         store_acc<S>(p, r, acc, acc_f, acc_out);
     }
 }
@@ -352,17 +374,19 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
     cp_async_commit();                                                  // A(z0)
     if (active) stage_pops<S>(p, sxy + nxy * z0, tid, T::NT, fin, mom, sF, sM);
     cp_async_commit();                                                  // P(z0)
+    float rest[S][3];
     for (int z = z0; z < z1; ++z) {
         cp_async_wait_all_but_newest();                                 // A(z) landed
         __syncthreads();
         const int kz = z - z0 + R;
         const long long r = sxy + nxy * z;
         float acc[S][3];
+        zero_acc<S>(acc);
         if (active) {
 #pragma unroll
             for (int a = 0; a < S; ++a) {
                 const float4 v = sR[a * T::NT + tid];
-                acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z;
+                rest[a][0] = v.x; rest[a][1] = v.y; rest[a][2] = v.z;
             }
         }
         if (z + 1 < z1) {
@@ -370,7 +394,11 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
             if (active) stage_rest<S>(p, r + nxy, tid, T::NT, frest, sR);
         }
         cp_async_commit();                                              // A(z + 1)
-        if (active) pass2_site<S, R, DRAG, kBY>(p, tab, sf, sg, kz, cidx, acc);
+        if (active) {
+            pass2_site<S, R, DRAG, kBY>(p, tab, sf, sg, kz, cidx, acc);
+#pragma unroll
+            for (int a = 0; a < S; ++a) add_rest(acc[a], make_float4(rest[a][0], rest[a][1], rest[a][2], 0.f));
+        }
         cp_async_wait_all_but_newest();                                 // P(z) landed (own slots only)
         if (active) {
             Centre<S> c;
@@ -387,6 +415,109 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
         cp_async_commit();                                              // P(z + 1)
     }
     cp_async_wait_all();
+}
+
+// ------------------------------------------------------------------ fused, with bulk tensor copies
+// The same per-site arithmetic as k_pass2_collide.  The site's own data of a
+// plane -- its 19 S populations, moments and rest force -- arrive as three
+// bulk tensor (TMA) copies of the block's 32 x 4 sites, issued by one thread
+// at the top of the plane and waited on (mbarrier, bounded) only before the
+// collision, so they land while the plane's shell sums run.  Shared layouts
+// are those of the cp.async variant: population (a, i) of thread t at
+// sF[(a * 19 + i) * 128 + t], moments and rest force at sM / sR[a * 128 + t].
+template <int S, int R>
+struct TmaTile {
+    using T = Tile<S, R>;
+    static constexpr size_t pad(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr uint32_t pops_bytes = (uint32_t)S * MLBI_Q * T::NT * 4;
+    static constexpr uint32_t v4_bytes = (uint32_t)S * T::NT * 16;
+    static constexpr size_t pops_off = pad(T::bytes);
+    static constexpr size_t mom_off = pops_off + pops_bytes;
+    static constexpr size_t rest_off = mom_off + v4_bytes;
+    static constexpr size_t bytes = rest_off + v4_bytes + 128;       // + alignment slack of the base
+    static constexpr uint32_t tx_bytes = pops_bytes + 2 * v4_bytes;
+};
+
+template <int S, int R, bool DRAG>
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2)
+    k_pass2_collide_tma(const mlbi_params p, const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
+                        const float4 *__restrict__ pst, float *__restrict__ fout, unsigned int *__restrict__ flags,
+                        const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_mom,
+                        const __grid_constant__ CUtensorMap map_rest)
+{
+    using T = Tile<S, R>;
+    using F = TmaTile<S, R>;
+    extern __shared__ float4 smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mem;
+    // the bulk copies want 128-byte aligned destinations
+    char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float4 *sf = reinterpret_cast<float4 *>(base);
+    float *sg = reinterpret_cast<float *>(sf + (size_t)T::NSLOT * S * T::PLANE);
+    float *sF = reinterpret_cast<float *>(base + F::pops_off);
+    float4 *sM = reinterpret_cast<float4 *>(base + F::mom_off);
+    float4 *sR = reinterpret_cast<float4 *>(base + F::rest_off);
+    __shared__ int s_fail;                                       // a wait gave up (read after a barrier)
+    const uint32_t bar = smem_u32(&bar_mem);
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int z1 = min(z0 + p.zchunk, p.nz);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const bool active = x < p.nx && y < p.ny;
+    const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    const int sxy = x + p.nx * y, nxy = p.nx * p.ny;
+    auto issue = [&](int z) {
+        mbar_expect_tx(bar, F::tx_bytes);
+        tma_load_4d(smem_u32(sF), &map_f, bar, x0, y0, z, 0);
+        tma_load_5d(smem_u32(sM), &map_mom, bar, 0, x0, y0, z, 0);
+        tma_load_5d(smem_u32(sR), &map_rest, bar, 0, x0, y0, z, 0);
+    };
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        s_fail = 0;
+    }
+    int xy[T::J];
+    stage_sites<S, R>(p, x0, y0, xy);
+    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    cp_async_commit();
+    __syncthreads();                                            // the barrier is initialised
+    if (tid == 0) issue(z0);
+    uint32_t phase = 0;
+    for (int z = z0; z < z1; ++z) {
+        cp_async_wait_all();
+        __syncthreads();              // ring planes up to z + R in; every thread is done with plane z - 1
+        if (s_fail) break;            // uniform: read after the barrier
+        if (tid == 0 && z > z0) issue(z);
+        const int kz = z - z0 + R;
+        if (z + 1 < z1) stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
+        cp_async_commit();
+        float acc[S][3];
+        zero_acc<S>(acc);
+        if (active) pass2_site<S, R, DRAG, kBY>(p, tab, sf, sg, kz, cidx, acc);
+        // each thread waits for the copies itself, so warps move on to their
+        // collisions independently; a wait that gives up marks the block failed,
+        // and every thread leaves at the next barrier
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!ok) {
+            s_fail = 1;
+            if (tid == 0) atomicOr(flags, MLBI_FLAG_TIMEOUT);
+            continue;
+        }
+        if (active) {
+            Centre<S> c;
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                const float4 v = sM[a * T::NT + tid];
+                c.dn[a] = v.x;
+                c.n[a] = p.nref[a] + v.x;
+                c.u[a][0] = v.y; c.u[a][1] = v.z; c.u[a][2] = v.w;
+                add_rest(acc[a], sR[a * T::NT + tid]);
+            }
+            collide_push<S>(p, x, y, z, sxy + nxy * z, c, acc, SharedPops{sF + tid, T::NT}, fout);
+        }
+    }
+    cp_async_wait_all();
+    if (s_fail && tid == 0) mbar_wait(bar, phase ^ 1u);       // one more bounded wait for the copy in flight
 }
 
 template <int S, int R, bool DRAG>
@@ -426,6 +557,19 @@ cudaError_t launch_pass2_collide_tiled(const mlbi_params &p, const mlbi_buffers 
     if constexpr (F::bytes > kMaxSharedPerBlock) {
         return cudaErrorInvalidValue;
     } else {
+    if constexpr (TmaTile<S, R>::bytes <= kMaxSharedPerBlock) {
+        if (b.maps && b.maps->ok) {
+            using G = TmaTile<S, R>;
+            auto k = k_pass2_collide_tma<S, R, DRAG>;
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
+            if (e != cudaSuccess) return e;
+            const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY),
+                         (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
+            k<<<g, dim3(kBX, kBY), G::bytes, s>>>(p, b.dg, b.table, b.pst, b.f[cur ^ 1], b.flags, b.maps->f[cur],
+                                                  b.maps->mom, b.maps->frest);
+            return cudaGetLastError();
+        }
+    }
     auto k = k_pass2_collide<S, R, DRAG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::bytes);
     if (e != cudaSuccess) return e;

@@ -67,15 +67,29 @@ __device__ __forceinline__ float pass2_point(float np, float nm, float jp, float
     return DRAG ? -(hp + hm) * sdu : fmaf(hp, jp, hm * jm);
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// Pass 1 accumulates in lane pairs so that one packed instruction (two IEEE
+// FP32 operations, each rounded as the scalar one) serves two sums:
+//   hf[q] = (F^hc_q, F^v_q) per component q, and the friction matrix as
+//   G[0] = (xx, yy), G[1] = (zz, xy), G[2] = (xz, yz).
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 // accumulate one point with a unit vector s given at run time
-__device__ __forceinline__ void add_pass1(float sx, float sy, float sz, float t, float sd, float wn, float (&hc)[3],
-                                          float (&fv)[3], float (&G)[6])
+__device__ __forceinline__ void add_pass1(float sx, float sy, float sz, float t, float sd, float wn, float2 (&hf)[3],
+                                          float2 (&G)[3])
 {
-    hc[0] = fmaf(sx, t, hc[0]); hc[1] = fmaf(sy, t, hc[1]); hc[2] = fmaf(sz, t, hc[2]);
-    fv[0] = fmaf(sx, sd, fv[0]); fv[1] = fmaf(sy, sd, fv[1]); fv[2] = fmaf(sz, sd, fv[2]);
-    const float wx = wn * sx, wy = wn * sy;
-    G[0] = fmaf(wx, sx, G[0]); G[1] = fmaf(wy, sy, G[1]); G[2] = fmaf(wn * sz, sz, G[2]);
-    G[3] = fmaf(wx, sy, G[3]); G[4] = fmaf(wx, sz, G[4]); G[5] = fmaf(wy, sz, G[5]);
+    const float2 tsd = f2(t, sd);
+    hf[0] = fma2(f2(sx, sx), tsd, hf[0]);
+    hf[1] = fma2(f2(sy, sy), tsd, hf[1]);
+    hf[2] = fma2(f2(sz, sz), tsd, hf[2]);
+    const float2 wxy = mul2(f2(wn, wn), f2(sx, sy));
+    const float wz = wn * sz;
+    G[0] = fma2(wxy, f2(sx, sy), G[0]);
+    G[1] = fma2(f2(wz, wxy.x), f2(sz, sy), G[1]);
+    G[2] = fma2(wxy, f2(sz, sz), G[2]);
 }
 
 // ------------------------------------------------------------------ neighbours from global memory
@@ -225,18 +239,31 @@ __device__ __forceinline__ void cube_add(float il, float t, float (&v)[3])
     if constexpr (cube_kz(K) != 0) v[2] = fmaf(cube_kz(K) * il, t, v[2]);
 }
 
-// G += wn s s^T for cube offset K
+// (F^hc, F^v) += s (t, sd) for cube offset K, one packed FMA per non-zero component
 template <int K>
-__device__ __forceinline__ void cube_add_ss(float il, float wn, float (&G)[6])
+__device__ __forceinline__ void cube_add2(float il, float2 tsd, float2 (&hf)[3])
+{
+    if constexpr (cube_kx(K) != 0) hf[0] = fma2(f2(cube_kx(K) * il, cube_kx(K) * il), tsd, hf[0]);
+    if constexpr (cube_ky(K) != 0) hf[1] = fma2(f2(cube_ky(K) * il, cube_ky(K) * il), tsd, hf[1]);
+    if constexpr (cube_kz(K) != 0) hf[2] = fma2(f2(cube_kz(K) * il, cube_kz(K) * il), tsd, hf[2]);
+}
+
+// G += wn s s^T for cube offset K, G packed as (xx, yy), (zz, xy), (xz, yz);
+// a pair with one zero entry is a scalar FMA on the other lane
+template <int K>
+__device__ __forceinline__ void cube_add_ss(float il, float wn, float2 (&G)[3])
 {
     constexpr int X = cube_kx(K), Y = cube_ky(K), Z = cube_kz(K);
     const float i2 = il * il;
-    if constexpr (X != 0) G[0] = fmaf(wn, i2, G[0]);
-    if constexpr (Y != 0) G[1] = fmaf(wn, i2, G[1]);
-    if constexpr (Z != 0) G[2] = fmaf(wn, i2, G[2]);
-    if constexpr (X * Y != 0) G[3] = fmaf(wn, X * Y * i2, G[3]);
-    if constexpr (X * Z != 0) G[4] = fmaf(wn, X * Z * i2, G[4]);
-    if constexpr (Y * Z != 0) G[5] = fmaf(wn, Y * Z * i2, G[5]);
+    if constexpr (X != 0 && Y != 0) G[0] = fma2(f2(wn, wn), f2(i2, i2), G[0]);
+    else if constexpr (X != 0) G[0].x = fmaf(wn, i2, G[0].x);
+    else if constexpr (Y != 0) G[0].y = fmaf(wn, i2, G[0].y);
+    if constexpr (Z != 0 && X * Y != 0) G[1] = fma2(f2(wn, wn), f2(i2, X * Y * i2), G[1]);
+    else if constexpr (Z != 0) G[1].x = fmaf(wn, i2, G[1].x);
+    else if constexpr (X * Y != 0) G[1].y = fmaf(wn, X * Y * i2, G[1].y);
+    if constexpr (X * Z != 0 && Y * Z != 0) G[2] = fma2(f2(wn, wn), f2(X * Z * i2, Y * Z * i2), G[2]);
+    else if constexpr (X * Z != 0) G[2].x = fmaf(wn, X * Z * i2, G[2].x);
+    else if constexpr (Y * Z != 0) G[2].y = fmaf(wn, Y * Z * i2, G[2].y);
 }
 
 // compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1
