@@ -49,6 +49,8 @@ def parse_args():
                          "taylor: the 3-species Taylor channel 512x64x64 between moving walls (--size sets the "
                          "channel's cross-section, the length is 8x)")
     ap.add_argument("--members", type=int, default=64, help="ensemble size")
+    ap.add_argument("--sweeps", type=int, default=1,
+                    help="Jacobi sweeps of the half step u* = u + a(u*)/2 (the method's default: one)")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the default decomposition")
     ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample extent for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -101,6 +103,7 @@ def algorithmic_bytes(kernel, S, npairs, has_fext=False, local_g=True):
         "k_gfield": 4 + g,                                       # dn read, g write
         "k_pass1": 16 + g + 12 + 16 + (12 if has_fext else 0),    # moments, g read; frest, p* write
         "k_pass2": 16 + g + 12 + 12,                               # p* = (n - n_ref, u*), g, frest read; acc write
+        "k_sweep": 16 + g + 16 + 12 + 16,                          # previous p*, g, own moments, frest read; p* write
         "k_collide": 76 + 16 + 12 + 76,                            # f, moments, acc read; f write
         "k_attraction": 4 + 12,                                     # n - n_ref read; G write
         # pass 2 fused with the collision: (n - n_ref, u*), g, frest, f, moments read; f write
@@ -150,8 +153,9 @@ def attraction_points(lat):
 # algorithmic FP32 operations per (ordered pair, stencil point):
 #   pass 1: pair value (2), hard core (7), velocity exchange (15), friction tensor (12)
 #   pass 2: pair value (2), velocity exchange (16)
+#   a further predictor sweep: pass 1 without the hard core (29)
 #   attraction: one 3-vector multiply-add per point of the full region (6)
-FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18, "k_pass2_collide": 18}
+FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18, "k_pass2_collide": 18, "k_sweep": 29}
 FLOPS_PER_ATTRACTION_POINT = 6
 # the surrogate network per site: 3^3 conv 2->32, 3^3 conv 32->32 (tensor cores), 1^3 conv 32->6
 FLOPS_PER_SURROGATE_SITE = 2 * (27 * 2 * 32 + 27 * 32 * 32 + 32 * 6)
@@ -162,7 +166,8 @@ def fp32_peak_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-KERNEL_SOURCE = {"k_pass1": "mlb_pass1.cu", "k_pass2": "mlb_pass2.cu", "k_pass2_collide": "mlb_pass2.cu",
+KERNEL_SOURCE = {"k_pass1": "mlb_pass1.cu", "k_sweep": "mlb_sweep.cu", "k_pass2": "mlb_pass2.cu",
+                 "k_pass2_collide": "mlb_pass2.cu",
                  "k_attraction": "mlb_attraction.cu", "k_surrogate": "mlb_surrogate.cu"}
 
 
@@ -350,6 +355,7 @@ def run_mlb(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     lat, n = workload(args.size, args.workload)
+    lat.predictor_sweeps = args.sweeps
     S, N = lat.nspecies, lat.nsites
     stream = torch.cuda.Stream(device=dev)
     sim = mlb.Simulation(lat, stream=stream)
@@ -492,7 +498,8 @@ def run_mlb(args, rank, world, local_rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sine-wave mixture)",
-           "config": config_dict(args.size, args.workload), "roofline": roof, "step_roofline": step_roof,
+           "config": dict(config_dict(args.size, args.workload), predictor_sweeps=args.sweeps),
+           "roofline": roof, "step_roofline": step_roof,
            "kernels": kernels, "gpu_launches": sim.launches_per_step() * args.steps * 1,
            "mlups": value / S, "clocks": clk, "e2e": e2e}
     if surrogate is not None:

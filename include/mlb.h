@@ -121,6 +121,24 @@ mlb_status mlb_set_fields(mlb_ctx *ctx, const double *n, const double *u);
  * fext: [S][3][N], or NULL to remove it. */
 mlb_status mlb_set_external_force(mlb_ctx *ctx, const double *fext);
 
+/* Number of Jacobi sweeps of the half step of the semi-implicit forcing (the
+ * force term of Eq. (evolution) entering at u + a/2): u* = u + a(u*)/2 is
+ * solved at every site by (I + Gamma/2) du = (F^hc + G + F^a + F^v)/2, with
+ * Gamma the local friction matrix and F^v the velocity exchange of
+ * Eqs. (gammaab), (viscousforce).  The first sweep takes the partners'
+ * velocities at u (the default, one sweep); each further sweep repeats the
+ * exchange and friction sums with the partners at the previous sweep's u*
+ * (one more pass over the contact shells, one more launch per step).  More
+ * sweeps approach the exactly solved half step: for unequal diameters the
+ * lattice mutual diffusion coefficient with one sweep lies about 0.6 %
+ * (sigma 1/1.5) above that of the exactly solved half step, with two about
+ * 0.02 %; the uniform sigma 1/1.5 mixture stays linearly stable to packing
+ * 0.3 with three sweeps (one sweep: about 0.2).  sweeps: 1..8.  The first
+ * request of more than one sweep allocates S x N float4 on the device
+ * (desc->dev_alloc), released by mlb_destroy.
+ * Errors: MLB_EINVAL (out of range, or MLB_FORCE_EXPLICIT set), MLB_ENOMEM. */
+mlb_status mlb_set_predictor_sweeps(mlb_ctx *ctx, int32_t sweeps);
+
 /* Advance nsteps >= 0 time steps of Eq. (evolution), Sec. II: per step the
  * moments (Eq. colonna), the contact values, the effective field
  * Phi = F^hc + G + F^v of Eqs. (splitforce), (potmeanforce), (gammaab) and
@@ -164,10 +182,11 @@ mlb_status mlb_get_moments(mlb_ctx *ctx, double *n, double *u);
  * state, Phi^a the effective field of Sec. III, Eqs. (splitforce) and
  * (potmeanforce) with the velocity exchange of Eqs. (gammaab) and
  * (viscousforce): acc [S][3][N], an FP64 host array owned by the caller.
- * Synchronous; errors MLB_EINVAL (acc NULL), MLB_ESTATE, MLB_ECUDA.  With the half-force shift it is F^hc + G + F^a plus the
- * velocity-exchange force at u* = u + du, where du solves
- * (I + Gamma/2) du = (F^hc + G + F^a + F^v(u))/2 at each site (one Jacobi
- * sweep of u* = u + a(u*)/2; Gamma = the local friction matrix). */
+ * With the half-force shift it is F^hc + G + F^a plus the velocity-exchange
+ * force at u*, the last of the Jacobi sweeps of u* = u + a(u*)/2 (see
+ * mlb_set_predictor_sweeps; the first solves (I + Gamma/2) du =
+ * (F^hc + G + F^a + F^v(u))/2 at each site, Gamma the local friction
+ * matrix).  Synchronous; errors MLB_EINVAL (acc NULL), MLB_ESTATE, MLB_ECUDA. */
 mlb_status mlb_get_acceleration(mlb_ctx *ctx, double *acc);
 
 /* FP64 global sums of the current state, the quantities the continuity

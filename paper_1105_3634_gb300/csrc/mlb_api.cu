@@ -46,8 +46,15 @@ struct mlb_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int> ev_kind;                   // kernel kind of pair k
     size_t ev_used = 0;
-    double prof_ms[8] = {0};
-    int64_t prof_count[8] = {0};
+    double prof_ms[16] = {0};
+    int64_t prof_count[16] = {0};
+    // Jacobi sweeps of the half step (mlb_set_predictor_sweeps); pst2 is the
+    // second (n - n_ref, u*) buffer the sweeps alternate with, allocated on
+    // the first request of more than one sweep; pst_final is where the last
+    // sweep of the current step left u*
+    int sweeps = 1;
+    float4 *pst2 = nullptr;
+    float4 *pst_final = nullptr;
     // work decomposition chosen by mlb_autotune (0 / -1: the defaults)
     int tuned_zchunk = 0;
     int tuned_split = -1;
@@ -427,10 +434,10 @@ mlb_status require_ready(mlb_ctx *c)
 
 enum {
     K_MOMENTS = 0, K_GFIELD = 1, K_PASS1 = 2, K_PASS2 = 3, K_COLLIDE = 4, K_ATTRACTION = 5, K_PASS2_COLLIDE = 6,
-    K_SURROGATE = 7, K_NKINDS = 8
+    K_SURROGATE = 7, K_SWEEP = 8, K_NKINDS = 9
 };
 const char *const kKernelNames[K_NKINDS] = {"k_moments", "k_gfield", "k_pass1", "k_pass2", "k_collide",
-                                            "k_attraction", "k_pass2_collide", "k_surrogate"};
+                                            "k_attraction", "k_pass2_collide", "k_surrogate", "k_sweep"};
 
 // event pair around one launch when profiling
 struct Timed {
@@ -457,9 +464,41 @@ struct Timed {
     }
 };
 
+mlb_status forces_pass1(mlb_ctx *c, bool sums);
+
+// Further Jacobi sweeps of the half step after pass 1 (pass 1 is the first):
+// u* alternates between b.pst and pst2; pst_final marks the last one.
+mlb_status sweeps(mlb_ctx *c)
+{
+    c->pst_final = c->b.pst;
+    if (!c->p.semi_implicit) return MLB_OK;
+    for (int k = 1; k < c->sweeps; ++k) {
+        float4 *next = c->pst_final == c->b.pst ? c->pst2 : c->b.pst;
+        Timed t(c, K_SWEEP);
+        MLB_CUDA(c, mlbi_launch_sweep(c->p, c->b, c->pst_final, next, c->stream));
+        c->pst_final = next;
+    }
+    return MLB_OK;
+}
+
 // The force passes of one step on the current populations; sums: the moment
 // pass also leaves the FP64 conservation sums of the state in b.sums.
 mlb_status forces(mlb_ctx *c, bool sums = false)
+{
+    mlb_status st = forces_pass1(c, sums);
+    if (st != MLB_OK) return st;
+    return sweeps(c);
+}
+
+// buffers for pass 2: u* where the last sweep left it
+mlbi_buffers pass2_buffers(const mlb_ctx *c)
+{
+    mlbi_buffers b = c->b;
+    if (c->pst_final) b.pst = c->pst_final;
+    return b;
+}
+
+mlb_status forces_pass1(mlb_ctx *c, bool sums)
 {
     if (c->p.local_g) {
         Timed t(c, K_MOMENTS);
@@ -511,12 +550,13 @@ bool split_collide(const mlb_ctx *c)
 // pass 2, collision and streaming of one step (after forces())
 mlb_status advance(mlb_ctx *c)
 {
+    const mlbi_buffers b = pass2_buffers(c);
     if (split_collide(c)) {
-        { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, nullptr, c->stream)); }
-        { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, c->b, c->cur, c->stream)); }
+        { Timed t(c, K_PASS2); MLB_CUDA(c, mlbi_launch_pass2(c->p, b, nullptr, c->stream)); }
+        { Timed t(c, K_COLLIDE); MLB_CUDA(c, mlbi_launch_collide(c->p, b, c->cur, c->stream)); }
     } else {
         Timed t(c, K_PASS2_COLLIDE);
-        MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, c->b, c->cur, c->stream));
+        MLB_CUDA(c, mlbi_launch_pass2_collide(c->p, b, c->cur, c->stream));
     }
     return MLB_OK;
 }
@@ -796,6 +836,28 @@ mlb_status mlb_set_external_force(mlb_ctx *c, const double *fext)
     return MLB_OK;
 }
 
+mlb_status mlb_set_predictor_sweeps(mlb_ctx *c, int32_t sweeps)
+{
+    MLB_GUARD(c);
+    if (sweeps < 1 || sweeps > 8) return fail(c, MLB_EINVAL, "predictor sweeps must be 1..8");
+    if (!c->p.semi_implicit && sweeps != 1)
+        return fail(c, MLB_EINVAL, "predictor sweeps need the semi-implicit forcing (MLB_FORCE_EXPLICIT is set)");
+    if (sweeps > 1 && !c->pst2) {
+        const size_t bytes = sizeof(float4) * (size_t)c->p.S * c->p.N;
+        void *ptr = nullptr;
+        if (c->desc.dev_alloc) {
+            ptr = c->desc.dev_alloc(bytes, c->desc.alloc_user);
+        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+        }
+        if (!ptr) return fail(c, MLB_ENOMEM, "could not allocate the second predictor buffer (%zu bytes)", bytes);
+        c->pst2 = (float4 *)ptr;
+    }
+    c->sweeps = sweeps;
+    ++c->version;
+    return MLB_OK;
+}
+
 mlb_status mlb_step(mlb_ctx *c, int64_t nsteps)
 {
     MLB_GUARD(c);
@@ -834,7 +896,7 @@ int32_t mlb_launches_per_step(const mlb_ctx *c)
 {
     if (!c) return 0;
     return (c->p.local_g ? 1 : 2) + (split_collide(c) ? 3 : 2) + (c->p.attr_r ? 1 : 0) +
-           (c->surr && c->surr_active ? 4 : 0);
+           (c->surr && c->surr_active ? 4 : 0) + (c->p.semi_implicit ? c->sweeps - 1 : 0);
 }
 
 const char *mlb_kernel_name(int32_t k)
@@ -903,7 +965,7 @@ mlb_status mlb_get_acceleration(mlb_ctx *c, double *acc)
     const long long N = c->p.N;
     st = forces(c);
     if (st != MLB_OK) return st;
-    MLB_CUDA(c, mlbi_launch_pass2(c->p, c->b, c->b.stage, c->stream));
+    MLB_CUDA(c, mlbi_launch_pass2(c->p, pass2_buffers(c), c->b.stage, c->stream));
     MLB_CUDA(c, cudaMemcpyAsync(acc, c->b.stage, sizeof(double) * S * 3 * N, cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     return check_flags(c);
@@ -1050,6 +1112,10 @@ void mlb_destroy(mlb_ctx *c)
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->surr_sums) cudaFree(c->surr_sums);
+    if (c->pst2) {
+        if (c->desc.dev_free) c->desc.dev_free(c->pst2, c->desc.alloc_user);
+        else cudaFree(c->pst2);
+    }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -150,6 +150,11 @@ cudaError_t mlbi_launch_moments(const mlbi_params &p, const mlbi_buffers &b, int
 cudaError_t mlbi_launch_pop_sums(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 cudaError_t mlbi_launch_gfield(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
+// one further Jacobi sweep of the half step: prev = the previous sweep's
+// (n - n_ref, u*) [S][N], next receives this sweep's (must differ from prev);
+// b.mom, b.dg, b.frest as left by pass 1
+cudaError_t mlbi_launch_sweep(const mlbi_params &p, const mlbi_buffers &b, const float4 *prev, float4 *next,
+                              cudaStream_t s);
 cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s,
                                   bool sums = false);

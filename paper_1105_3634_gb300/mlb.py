@@ -67,6 +67,8 @@ def _load():
     L.mlb_set_external_force.restype = st
     L.mlb_step.argtypes = [vp, ctypes.c_int64]
     L.mlb_step.restype = st
+    L.mlb_set_predictor_sweeps.argtypes = [vp, ctypes.c_int32]
+    L.mlb_set_predictor_sweeps.restype = st
     L.mlb_synchronize.argtypes = [vp]
     L.mlb_synchronize.restype = st
     L.mlb_get_moments.argtypes = [vp, dp, dp]
@@ -204,8 +206,6 @@ class Simulation:
 
     def __init__(self, lat, stream=None, torch_alloc: bool = True, split_collide: bool = False):
         import torch
-        if getattr(lat, "predictor_sweeps", 1) != 1:
-            raise ValueError("the library's semi-implicit step takes one predictor sweep")
         self.lat = lat
         self.S = lat.nspecies
         self.N = lat.nsites
@@ -238,6 +238,9 @@ class Simulation:
         if np.any(eps != 0):
             self._check(lib.mlb_set_interactions(self.ctx, _dp(eps),
                                                  _dp(np.ascontiguousarray(lat.lambda_c, np.float64))))
+        sweeps = int(getattr(lat, "predictor_sweeps", 1))
+        if sweeps != 1:
+            self._check(lib.mlb_set_predictor_sweeps(self.ctx, sweeps))
 
     # -- plumbing
     def _check(self, st):

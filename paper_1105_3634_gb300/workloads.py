@@ -38,7 +38,7 @@ class Lattice:
     wall_u_hi: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     drag_only: bool = False
     force_scheme: str = "semi_implicit"        # or "explicit" (forward Euler forcing)
-    predictor_sweeps: int = 1                  # Jacobi sweeps of the half step (the library takes one)
+    predictor_sweeps: int = 1                  # Jacobi sweeps of the half step u* = u + a(u*)/2
 
     def __post_init__(self):
         S = len(self.sigma)

@@ -425,3 +425,34 @@ def test_monitored_steps_report_the_conservation_sums(gpu):
     assert np.array_equal(a.populations()[0].view(np.uint32), b.populations()[0].view(np.uint32))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case,sweeps", [
+    ("config1", 2),              # the benchmark physics, cube tiles, 500 steps
+    ("attraction", 3),           # sigma = 2/3 with tails: reach-3 tiles, the column attraction kernel
+    ("drag_walls", 2),           # drag only (partner u* at the site), reach-2 tiles, walls normal to z
+    ("reach4", 2),               # the global-memory passes
+])
+def test_predictor_sweeps_match_the_oracle(gpu, orc, case, sweeps):
+    """Further Jacobi sweeps of the half step on the GPU against the oracle
+    with the same sweeps (partners at the previous sweep's u*)."""
+    if case == "config1":
+        lat, n = W.binary_config1()
+        u, cps = None, (0, 1, 100, 500)
+    elif case == "attraction":
+        lat, n = W.binary_attraction((18, 16, 17), seed=11)
+        u, cps = None, (0, 1, 20, 60)
+    elif case == "drag_walls":
+        lat = W.Lattice(shape=(36, 10, 12), sigma=[2.0, 1.5], drag_only=True, wall_axis=2,
+                        wall_u_lo=(-0.02, 0.0, 0.0), wall_u_hi=(0.02, 0.0, 0.0))
+        n = W.noise(lat, W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5]), 0.03, seed=7)
+        u, cps = W.random_velocities(lat, 0.01, seed=5), (0, 1, 40)
+    else:
+        lat = W.Lattice(shape=(20, 16, 14), sigma=[4.0, 3.0], tau=0.9)
+        n = W.noise(lat, W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5]), 0.02, seed=41)
+        u, cps = W.random_velocities(lat, 0.005, seed=42), (0, 1, 40)
+    lat.predictor_sweeps = sweeps
+    rep = []
+    w = run_pair(gpu, orc, lat, n, u, checkpoints=cps, report=rep)
+    print(case, sweeps, rep)
+    assert ok(w), w
