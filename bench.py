@@ -49,6 +49,9 @@ def parse_args():
                          "taylor: the 3-species Taylor channel 512x64x64 between moving walls (--size sets the "
                          "channel's cross-section, the length is 8x)")
     ap.add_argument("--members", type=int, default=64, help="ensemble size")
+    ap.add_argument("--meanfield", choices=["fp32", "bf16", "bf16_1pass"], default="fp32",
+                    help="attractive mean field: FP32 column sums, or the tensor-core band product in BF16 "
+                         "(compensated hi/lo, or the single hi product)")
     ap.add_argument("--sweeps", type=int, default=1,
                     help="Jacobi sweeps of the half step u* = u + a(u*)/2 (the method's default: one)")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the default decomposition")
@@ -159,6 +162,36 @@ FLOPS_PER_SHELL_POINT = {"k_pass1": 36, "k_pass2": 18, "k_pass2_collide": 18, "k
 FLOPS_PER_ATTRACTION_POINT = 6
 # the surrogate network per site: 3^3 conv 2->32, 3^3 conv 32->32 (tensor cores), 1^3 conv 32->6
 FLOPS_PER_SURROGATE_SITE = 2 * (27 * 2 * 32 + 27 * 32 * 32 + 32 * 6)
+
+
+def attraction_columns(lat):
+    """Columns (dx, dy) of the attraction regions: the offsets of any pair's
+    sigma_ab <= |d| <= lambda_c sigma_ab projected onto the (x, y) plane."""
+    cols = set()
+    S = len(lat.sigma)
+    for a in range(S):
+        for b in range(S):
+            if lat.eps[a][b] == 0.0:
+                continue
+            s = 0.5 * (lat.sigma[a] + lat.sigma[b])
+            rc = lat.lambda_c[a][b] * s
+            R = int(math.floor(rc + 1e-9))
+            for dz in range(-R, R + 1):
+                for dy in range(-R, R + 1):
+                    for dx in range(-R, R + 1):
+                        q = dx * dx + dy * dy + dz * dz
+                        if q > 0 and s * s <= q <= rc * rc:
+                            cols.add((dx, dy))
+    return len(cols)
+
+
+def tensor_flops_attraction(lat, products):
+    """MMA flops of one tensor-core attraction launch: per tile of 128 x sites
+    and 16 planes, per column, M 128 x N 48 S x K 32 S, times the products."""
+    S = lat.nspecies
+    nx, ny, nz = lat.shape
+    tiles = -(-nx // 128) * ny * -(-nz // 16)
+    return tiles * attraction_columns(lat) * products * 2.0 * 128 * (48 * S) * (32 * S)
 
 
 def fp32_peak_tflops(sm_mhz=2070.0):
@@ -356,6 +389,7 @@ def run_mlb(args, rank, world, local_rank):
 
     lat, n = workload(args.size, args.workload)
     lat.predictor_sweeps = args.sweeps
+    lat.meanfield = args.meanfield
     S, N = lat.nspecies, lat.nsites
     stream = torch.cuda.Stream(device=dev)
     sim = mlb.Simulation(lat, stream=stream)
@@ -450,6 +484,14 @@ def run_mlb(args, rank, world, local_rank):
         fl = None
         if name in FLOPS_PER_SHELL_POINT:
             fl = FLOPS_PER_SHELL_POINT[name] * pts * N
+        elif name == "k_attraction" and args.meanfield != "fp32":
+            fl = FLOPS_PER_ATTRACTION_POINT * attraction_points(lat) * N
+            tfl = tensor_flops_attraction(lat, 3 if args.meanfield == "bf16" else 1)
+            k["tensor_flops_per_launch"] = tfl
+            k["achieved_tensor_tflops"] = tfl / (per_launch_ms * 1e-3) / 1e12
+            k["flops_note"] = ("algorithmic: the direct lattice sum (6 flops per region point); tensor: the BF16 "
+                               "MMAs executed (band matrices along z, zeros included; %s)"
+                               % ("hi*hi + hi*lo + lo*hi" if args.meanfield == "bf16" else "hi*hi"))
         elif name == "k_attraction":
             fl = FLOPS_PER_ATTRACTION_POINT * attraction_points(lat) * N
             k["flops_note"] = ("direct lattice sum, one 3-vector FMA per region point; the column kernel "
@@ -475,6 +517,12 @@ def run_mlb(args, rank, world, local_rank):
            "traffic": committed_traffic(top, args.size, args.workload)}
     # the binding resource of the dominant kernel: the larger fraction of its peak
     roof = alu if (alu["frac"] or 0.0) > (hbm["frac"] or 0.0) else hbm
+    if top == "k_attraction" and args.meanfield != "fp32":
+        tpk = measured_peak_bf16()
+        roof = {"kernel": top, "bound": "tensor", "achieved": kt["achieved_tensor_tflops"], "peak": tpk,
+                "peak_kind": "measured (MEASURED_PEAKS.json bf16_tflops, burst)", "unit": "TFLOP/s",
+                "frac": kt["achieved_tensor_tflops"] / tpk,
+                "traffic": committed_traffic(top, args.size, args.workload)}
     if top == "k_surrogate":
         tpk = measured_peak_bf16()
         roof = {"kernel": top, "bound": "tensor", "achieved": kt["achieved_tflops"], "peak": tpk,
@@ -498,7 +546,8 @@ def run_mlb(args, rank, world, local_rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sine-wave mixture)",
-           "config": dict(config_dict(args.size, args.workload), predictor_sweeps=args.sweeps),
+           "config": dict(config_dict(args.size, args.workload), predictor_sweeps=args.sweeps,
+                          meanfield=args.meanfield),
            "roofline": roof, "step_roofline": step_roof,
            "kernels": kernels, "gpu_launches": sim.launches_per_step() * args.steps * 1,
            "mlups": value / S, "clocks": clk, "e2e": e2e}

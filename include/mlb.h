@@ -65,6 +65,16 @@ typedef enum {
 #define MLB_SPLIT_COLLIDE   4u   /* launch pass 2 and the collision separately (the acceleration
                                     field is stored every step); default: one fused launch.
                                     Both give bitwise-identical populations. */
+#define MLB_MEANFIELD_BF16  8u   /* the attractive mean field G (Sec. III, Eq. potmeanforce) as a
+                                    band-matrix product along z on the tensor cores: BF16 operands
+                                    split hi + lo (densities and kernel), FP32 accumulation, the
+                                    compensated product hi*hi + hi*lo + lo*hi (relative error of G
+                                    about 1e-5).  Needs 1 or 2 species, an attraction reach of 1..8,
+                                    nz % 8 == 0 and no walls normal to z (mlb_set_interactions
+                                    returns MLB_EINVAL otherwise).  Default: FP32 column sums. */
+#define MLB_MEANFIELD_BF16_1PASS 16u  /* with MLB_MEANFIELD_BF16: the single product hi*hi only
+                                    (about a third of the tensor work; relative error of G of
+                                    order 1e-3) */
 
 typedef struct {
     int32_t nx, ny, nz;          /* lattice extents, each >= 1 */

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmlb.so")
-SOURCES = ["mlb_api.cu", "mlb_kernels.cu", "mlb_pass1.cu", "mlb_sweep.cu", "mlb_pass2.cu", "mlb_attraction.cu", "mlb_surrogate.cu",
+SOURCES = ["mlb_api.cu", "mlb_kernels.cu", "mlb_pass1.cu", "mlb_sweep.cu", "mlb_pass2.cu", "mlb_attraction.cu", "mlb_attraction_tc.cu", "mlb_surrogate.cu",
            "mlb_noalloc.cu", "mlb_copy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -55,6 +55,11 @@ struct mlb_ctx {
     int sweeps = 1;
     float4 *pst2 = nullptr;
     float4 *pst_final = nullptr;
+    // tensor-core attraction (MLB_MEANFIELD_BF16): tables in their own device
+    // allocation, rebuilt with the stencils
+    mlbi_tc_tables tc{};
+    void *tc_mem = nullptr;
+    size_t tc_bytes = 0;
     // work decomposition chosen by mlb_autotune (0 / -1: the defaults)
     int tuned_zchunk = 0;
     int tuned_split = -1;
@@ -172,6 +177,137 @@ void encode_maps(mlb_ctx *c)
 bool canonical(int dx, int dy, int dz)
 {
     return dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+}
+
+// FP32 -> BF16 bits, round to nearest even (finite values)
+uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+void *ctx_alloc(mlb_ctx *c, size_t bytes)
+{
+    void *ptr = nullptr;
+    if (c->desc.dev_alloc) return c->desc.dev_alloc(bytes, c->desc.alloc_user);
+    return cudaMalloc(&ptr, bytes) == cudaSuccess ? ptr : nullptr;
+}
+void ctx_free(mlb_ctx *c, void *ptr)
+{
+    if (!ptr) return;
+    if (c->desc.dev_free) c->desc.dev_free(ptr, c->desc.alloc_user);
+    else cudaFree(ptr);
+}
+
+// Tables of the tensor-core attraction: the columns (dx, dy) of every pair's
+// region sigma_ab <= |d| <= lambda_c sigma_ab, sorted by dy then dx, and per
+// column the B operand of the band product along z, hi and lo BF16 parts of
+// K_ab(dx, dy, z' - z)_c at row k = 32 b + z' - z0 + 8, column
+// n = 16 (3 a + c) + z, in the K-major layout [k / 8][n][k % 8].
+mlb_status build_tc_tables(mlb_ctx *c)
+{
+    const mlbi_params &p = c->p;
+    const int S = p.S, R = p.attr_r;
+    const int N = 48 * S, K = 32 * S, KC = K / 8;
+    auto rc_of = [&](int a, int b) { return c->lambda_c[a * S + b] * 0.5 * (c->sigma[a] + c->sigma[b]); };
+    auto kernel = [&](int a, int b, int dx, int dy, int dz, int comp) {
+        const double e = c->eps[a * S + b], sab = 0.5 * (c->sigma[a] + c->sigma[b]), rc = rc_of(a, b);
+        const double q = (double)(dx * dx + dy * dy + dz * dz);
+        if (e == 0.0 || q == 0.0 || q < sab * sab || q > rc * rc) return 0.0;
+        const double d[3] = {(double)dx, (double)dy, (double)dz};
+        return 6.0 * e * std::pow(sab, 6.0) / (q * q * q * q) * d[comp];
+    };
+    std::vector<int2> cols;
+    std::vector<int> row_start;
+    for (int dy = -R; dy <= R; ++dy) {
+        bool row = false;
+        for (int dx = -R; dx <= R; ++dx) {
+            bool any = false;
+            for (int a = 0; a < S && !any; ++a)
+                for (int b = 0; b < S && !any; ++b)
+                    for (int dz = -R; dz <= R && !any; ++dz) any = kernel(a, b, dx, dy, dz, 0) != 0.0 ||
+                                                                  kernel(a, b, dx, dy, dz, 1) != 0.0 ||
+                                                                  kernel(a, b, dx, dy, dz, 2) != 0.0;
+            if (!any) continue;
+            if (!row) row_start.push_back((int)cols.size());
+            row = true;
+            cols.push_back(make_int2(dx, dy));
+        }
+    }
+    row_start.push_back((int)cols.size());
+    const size_t colb = mlbi_attraction_tc_column_bytes(S);
+    std::vector<uint16_t> w(cols.size() * colb / 2, 0);
+    for (size_t ci = 0; ci < cols.size(); ++ci) {
+        uint16_t *hi = w.data() + ci * colb / 2, *lo = hi + (size_t)KC * N * 8;
+        for (int k = 0; k < K; ++k)
+            for (int n = 0; n < N; ++n) {
+                const int b = k / 32, zz = k % 32, a = n / 48, comp = (n / 16) % 3, z = n % 16;
+                const double v = kernel(a, b, cols[ci].x, cols[ci].y, zz - 8 - z, comp);
+                const uint16_t h = bf16_bits((float)v);
+                const uint16_t l = bf16_bits((float)(v - (double)bf16_value(h)));
+                const size_t at = ((size_t)(k / 8) * N + n) * 8 + k % 8;
+                hi[at] = h;
+                lo[at] = l;
+            }
+    }
+    int nxp = 0, nyp = 0;
+    mlbi_attraction_tc_padded(p, &nxp, &nyp);
+    const size_t qb = align256(sizeof(uint16_t) * (size_t)S * nxp * nyp * p.nz);
+    const size_t need = align256(w.size() * 2) + align256(cols.size() * sizeof(int2)) +
+                        align256(row_start.size() * sizeof(int)) + 2 * qb;
+    if (need > c->tc_bytes) {
+        ctx_free(c, c->tc_mem);
+        c->tc_mem = ctx_alloc(c, need);
+        c->tc_bytes = c->tc_mem ? need : 0;
+        if (!c->tc_mem) return fail(c, MLB_ENOMEM, "tensor-core attraction tables (%zu bytes)", need);
+    }
+    char *m = (char *)c->tc_mem;
+    c->tc.weights = m; m += align256(w.size() * 2);
+    c->tc.cols = (int2 *)m; m += align256(cols.size() * sizeof(int2));
+    c->tc.row_start = (int *)m; m += align256(row_start.size() * sizeof(int));
+    c->tc.qhi = m; m += qb;
+    c->tc.qlo = m;
+    c->tc.ncols = (int)cols.size();
+    c->tc.nrows = (int)row_start.size() - 1;
+    c->tc.pass3 = (c->desc.flags & MLB_MEANFIELD_BF16_1PASS) ? 0 : 1;
+    // tensor maps of the padded copies: dims (z, b, xp, yp), box (8 planes, 1, 144 sites, 1)
+    c->tc.maps_ok = 0;
+    {
+        EncodeTiledFn fn = encode_tiled();
+        if (!fn) return fail(c, MLB_EINVAL, "the BF16 mean field needs cuTensorMapEncodeTiled from the driver");
+        const cuuint64_t dims[4] = {(cuuint64_t)p.nz, (cuuint64_t)S, (cuuint64_t)nxp, (cuuint64_t)nyp};
+        const cuuint64_t strides[3] = {(cuuint64_t)p.nz * 2, (cuuint64_t)S * p.nz * 2, (cuuint64_t)nxp * S * p.nz * 2};
+        const cuuint32_t box[4] = {8, 1, 144, 1}, ones[4] = {1, 1, 1, 1};
+        void *srcs[2] = {c->tc.qhi, c->tc.qlo};
+        CUtensorMap *maps[2] = {&c->tc.map_hi, &c->tc.map_lo};
+        for (int k = 0; k < 2; ++k)
+            if (fn(maps[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, srcs[k], dims, strides, box, ones,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return fail(c, MLB_EINVAL, "could not encode the tensor maps of the BF16 density copies");
+        c->tc.maps_ok = 1;
+    }
+    MLB_CUDA(c, cudaMemcpyAsync(c->tc.weights, w.data(), w.size() * 2, cudaMemcpyHostToDevice, c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(c->tc.cols, cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(c->tc.row_start, row_start.data(), row_start.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MLB_OK;
+}
+
+bool use_tc_attraction(const mlb_ctx *c)
+{
+    return (c->desc.flags & MLB_MEANFIELD_BF16) && c->p.attr_r && c->tc.ncols > 0;
 }
 
 // Rebuild every stencil table and the parameter block from species,
@@ -410,6 +546,15 @@ mlb_status rebuild(mlb_ctx *c)
     MLB_CUDA(c, cudaMemcpyAsync((void *)c->b.table, tab.data(), tab.size() * sizeof(mlbi_entry),
                                 cudaMemcpyHostToDevice, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->tc.ncols = 0;
+    if ((c->desc.flags & MLB_MEANFIELD_BF16) && p.has_attraction) {
+        if (!mlbi_attraction_tc_supported(p))
+            return fail(c, MLB_EINVAL,
+                        "the BF16 tensor-core mean field needs 1 or 2 species, an attraction reach of 1..8, "
+                        "nz a multiple of 8 and no walls normal to z");
+        mlb_status st = build_tc_tables(c);
+        if (st != MLB_OK) return st;
+    }
     ++c->version;
     return MLB_OK;
 }
@@ -509,7 +654,8 @@ mlb_status forces_pass1(mlb_ctx *c, bool sums)
     }
     if (c->p.attr_r) {
         Timed t(c, K_ATTRACTION);
-        MLB_CUDA(c, mlbi_launch_attraction(c->p, c->b, c->stream));
+        if (use_tc_attraction(c)) MLB_CUDA(c, mlbi_launch_attraction_tc(c->p, c->b, c->tc, c->stream));
+        else MLB_CUDA(c, mlbi_launch_attraction(c->p, c->b, c->stream));
     }
     if (c->surr && c->surr_active) {
         // the network's F^hc into attr; every surr_every steps the exact pass 1
@@ -612,7 +758,11 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     if (!(d->tau > 0.5) || !std::isfinite(d->tau)) return bad("tau must be finite and > 1/2");
     if (!(std::fabs(d->kT - kCs2) < 1e-12)) return bad("kT must be 1/3 (D3Q19 lattice units)");
     if (!(c->desc.kappa >= 0.0) || !std::isfinite(c->desc.kappa)) return bad("kappa must be >= 0");
-    if (d->flags & ~(MLB_DRAG_ONLY | MLB_FORCE_EXPLICIT | MLB_SPLIT_COLLIDE)) return bad("unknown flag bits");
+    if (d->flags & ~(MLB_DRAG_ONLY | MLB_FORCE_EXPLICIT | MLB_SPLIT_COLLIDE | MLB_MEANFIELD_BF16 |
+                     MLB_MEANFIELD_BF16_1PASS))
+        return bad("unknown flag bits");
+    if ((d->flags & MLB_MEANFIELD_BF16_1PASS) && !(d->flags & MLB_MEANFIELD_BF16))
+        return bad("MLB_MEANFIELD_BF16_1PASS needs MLB_MEANFIELD_BF16");
     if (d->wall_axis >= 0) {
         if (d->wall_u_lo[d->wall_axis] != 0.0 || d->wall_u_hi[d->wall_axis] != 0.0)
             return bad("wall velocities must be tangential to the wall");
@@ -1112,10 +1262,8 @@ void mlb_destroy(mlb_ctx *c)
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->surr_sums) cudaFree(c->surr_sums);
-    if (c->pst2) {
-        if (c->desc.dev_free) c->desc.dev_free(c->pst2, c->desc.alloc_user);
-        else cudaFree(c->pst2);
-    }
+    ctx_free(c, c->pst2);
+    ctx_free(c, c->tc_mem);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -116,6 +116,21 @@ struct mlbi_maps {
     int ok;
 };
 
+// Tables of the tensor-core attraction (mlb_attraction_tc.cu), device memory
+// owned by the context: per column (dx, dy), sorted by dy then dx, the B
+// operands hi and lo; the columns and the first column of every dy row; the
+// BF16 hi / lo copies of n - n_ref in the layout [y][x][b][z].
+struct mlbi_tc_tables {
+    void *weights;                   // [ncols][hi, lo][K / 8][N][8] BF16
+    int2 *cols;                      // [ncols] (dx, dy)
+    int *row_start;                  // [nrows + 1]
+    void *qhi, *qlo;                 // [nyp][nxp][S][nz] BF16 each (padded, mlbi_attraction_tc_padded)
+    CUtensorMap map_hi, map_lo;      // 4D tensor maps of qhi / qlo: (z, b, xp, yp), box (8, 1, 144, 1)
+    int maps_ok;
+    int ncols, nrows;
+    int pass3;                       // 1: compensated hi/lo product, 0: hi only
+};
+
 // Device buffers of one context (all carved from one allocation).
 struct mlbi_buffers {
     float *f[2];                     // [S][19][N] populations minus w_i n_ref
@@ -155,6 +170,15 @@ cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaS
 // b.mom, b.dg, b.frest as left by pass 1
 cudaError_t mlbi_launch_sweep(const mlbi_params &p, const mlbi_buffers &b, const float4 *prev, float4 *next,
                               cudaStream_t s);
+// tensor-core attraction: whether the lattice and species suit it (S <= 2,
+// reach <= 8, no walls normal to z, nz % 8 == 0), bytes of one column's B
+// operands, and the launch (prep + implicit GEMM) writing b.attr
+bool mlbi_attraction_tc_supported(const mlbi_params &p);
+size_t mlbi_attraction_tc_column_bytes(int S);
+// padded extents of the BF16 density copies (an 8-site halo in x and y, x up to whole tiles)
+void mlbi_attraction_tc_padded(const mlbi_params &p, int *nxp, int *nyp);
+cudaError_t mlbi_launch_attraction_tc(const mlbi_params &p, const mlbi_buffers &b, const mlbi_tc_tables &t,
+                                      cudaStream_t s);
 cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s,
                                   bool sums = false);

@@ -23,6 +23,8 @@ MLB_MAX_SPECIES = 4
 MLB_DRAG_ONLY = 1
 MLB_FORCE_EXPLICIT = 2
 MLB_SPLIT_COLLIDE = 4
+MLB_MEANFIELD_BF16 = 8
+MLB_MEANFIELD_BF16_1PASS = 16
 
 STATUS = {0: "MLB_OK", 1: "MLB_EINVAL", 2: "MLB_ENOMEM", 3: "MLB_ECUDA", 4: "MLB_ENUMERIC",
           5: "MLB_ETIMEOUT", 6: "MLB_ESTATE"}
@@ -218,6 +220,10 @@ class Simulation:
         d.wall_axis = lat.wall_axis
         d.flags = (MLB_DRAG_ONLY if lat.drag_only else 0) | (
             MLB_FORCE_EXPLICIT if lat.force_scheme == "explicit" else 0) | (MLB_SPLIT_COLLIDE if split_collide else 0)
+        mf = getattr(lat, "meanfield", "fp32")
+        if mf not in ("fp32", "bf16", "bf16_1pass"):
+            raise ValueError(f"meanfield must be fp32, bf16 or bf16_1pass, not {mf!r}")
+        d.flags |= (MLB_MEANFIELD_BF16 if mf != "fp32" else 0) | (MLB_MEANFIELD_BF16_1PASS if mf == "bf16_1pass" else 0)
         for k in range(3):
             d.wall_u_lo[k] = lat.wall_u_lo[k]
             d.wall_u_hi[k] = lat.wall_u_hi[k]
@@ -352,12 +358,13 @@ class Simulation:
 
     def profile_read(self):
         """{kernel name: (total ms, launches)} since the last read."""
-        ms = np.zeros(8)
-        cnt = np.zeros(8, np.int64)
-        k = lib.mlb_profile_read(self.ctx, _dp(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 8)
+        cap = 32
+        ms = np.zeros(cap)
+        cnt = np.zeros(cap, np.int64)
+        k = lib.mlb_profile_read(self.ctx, _dp(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap)
         if k < 0:
             raise MLBError(6, "profile read failed")
-        return {lib.mlb_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
+        return {lib.mlb_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(min(k, cap))}
 
 
 class Batch:

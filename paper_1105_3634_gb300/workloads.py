@@ -39,6 +39,8 @@ class Lattice:
     drag_only: bool = False
     force_scheme: str = "semi_implicit"        # or "explicit" (forward Euler forcing)
     predictor_sweeps: int = 1                  # Jacobi sweeps of the half step u* = u + a(u*)/2
+    meanfield: str = "fp32"                    # attraction on the GPU: "fp32" column sums, "bf16"
+                                               # compensated tensor-core product, "bf16_1pass" hi*hi only
 
     def __post_init__(self):
         S = len(self.sigma)
