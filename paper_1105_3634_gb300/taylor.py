@@ -164,6 +164,42 @@ def measure_dispersion(mlb, lat: W.Lattice, n0: Sequence[float], U: float, nu: f
     return _fit_rate(np.array(ts), np.array(amps)) / (kx * kx), float(np.mean(flows))
 
 
+def couette_flow(lat: W.Lattice) -> np.ndarray:
+    """The steady profile between the walls normal to y (halfway bounce-back at
+    -1/2 and ny - 1/2): u_x linear from the lower wall's velocity to the upper's,
+    every species."""
+    ny = lat.shape[1]
+    y = W.coordinate(lat, 1)
+    lo, hi = lat.wall_u_lo[0], lat.wall_u_hi[0]
+    u = np.zeros((lat.nspecies, 3, lat.nsites))
+    u[:, 0, :] = (lo + (hi - lo) * (y + 0.5) / ny)[None, :]
+    return u
+
+
+def measure_channel_dispersion(mlb, lat: W.Lattice, n0: Sequence[float], species: int, delta: float = 0.5,
+                               t0: int = 100, t1: int = 600, every: int = 50) -> float:
+    """D_eff of one species between moving walls normal to y (the Taylor
+    channel): n^s = n0_s (1 + delta sin(k_x x)) with the other species uniform,
+    the flow started from the Couette profile of the walls; the decay rate of
+    the k_x mode of n^s (averaged over y, z) divided by k_x^2.  For a dilute
+    solute delta may be large (its own density barely acts on the solvents)."""
+    n = np.array([np.full(lat.nsites, v) for v in n0])
+    x = W.coordinate(lat, 0)
+    kx = 2.0 * math.pi / lat.shape[0]
+    n[species] = n0[species] * (1.0 + delta * np.sin(kx * x))
+    sim = _sim(mlb, lat, n, couette_flow(lat))
+    ts, amps = [], []
+    t = 0
+    for target in range(t0, t1 + 1, every):
+        sim.step(target - t)
+        t = target
+        nn, _ = sim.moments()
+        ts.append(t)
+        amps.append(_mode(lat, nn[species], 0))
+    sim.close()
+    return _fit_rate(np.array(ts), np.array(amps)) / (kx * kx)
+
+
 def dispersion_curve(mlb, lat: W.Lattice, n0: Sequence[float], Us: Sequence[float], **kw) -> Dict:
     """D(0), nu, and for every U: the measured D_eff, the flow reached, Pe, the
     exact passive-scalar D_eff and Eq. taylordiff."""
@@ -178,3 +214,56 @@ def dispersion_curve(mlb, lat: W.Lattice, n0: Sequence[float], Us: Sequence[floa
                      "D_eff_passive_scalar": passive_scalar_rate(D0, Ur, kx, ky),
                      "D_eff_eq_taylordiff": taylor_formula(D0, Ur, lat.shape[1])})
     return {"D0": D0, "nu": nu, "rows": rows}
+
+
+# ------------------------------------------------------------------ the paper's experiment (Sec. V, Figs. 3-5)
+def paper_lattice(packing: float, Lx: int, Ly: int = 40, Lz: int = 40, tau: float = 1.0):
+    """The mixture of Figs. 3-5: sigma_AA = 8, sigma_BB = 4 (contact shells of
+    762 points for A-A), equal mole fractions c_0 = 0.5, total packing xi_3
+    (0.211 or 0.332), box L_x x 40 x 40, periodic; tau is not stated (1)."""
+    lat = W.Lattice(shape=(Lx, Ly, Lz), sigma=[8.0, 4.0], tau=tau)
+    return lat, W.densities_from_packing(packing, lat.sigma, [0.5, 0.5])
+
+
+def paper_curve(mlb, packing: float, Lx: int, pes: Sequence[float], Ly: int = 40, Lz: int = 40) -> Dict:
+    """Fig. 5: D_eff against Pe = U L_y / (2 D) for the Fig. 3 mixture.  D(0)
+    is measured first (no flow), the flow amplitude for each target Pe is
+    U = 2 D(0) Pe / L_y, and every fit spans 0.3 to 2.5 decay times of the
+    wave; rows give the Pe reached, D_eff / D(0), the exact passive-scalar
+    ratio for the flow reached and Eq. taylordiff's 1 + Pe^2 / (2 pi^2)."""
+    lat, n0 = paper_lattice(packing, Lx, Ly, Lz)
+    kx = 2.0 * math.pi / Lx
+    ky = 2.0 * math.pi / Ly
+
+    def window(D):
+        rate = D * kx * kx
+        t0, t1 = max(5, int(0.3 / rate)), max(40, int(2.5 / rate))
+        return dict(t0=t0, t1=t1, every=max(1, (t1 - t0) // 12))
+
+    D_guess, _ = measure_dispersion(mlb, lat, n0, 0.0, 0.0, t0=10, t1=60, every=5)
+    D0, _ = measure_dispersion(mlb, lat, n0, 0.0, 0.0, **window(D_guess))
+    nu = measure_viscosity(mlb, lat, n0)
+    rows = []
+    for pe in pes:
+        U = 2.0 * D0 * pe / Ly
+        Deff, Ur = measure_dispersion(mlb, lat, n0, U, nu, **window(D0 * (1.0 + pe * pe / (2 * math.pi ** 2))))
+        pe_r = peclet(D0, Ur, Ly)
+        rows.append({"Pe_target": pe, "U": U, "Pe": pe_r, "D_eff": Deff, "ratio": Deff / D0,
+                     "ratio_passive_scalar": passive_scalar_rate(D0, Ur, kx, ky) / D0,
+                     "ratio_eq_taylordiff": 1.0 + pe_r * pe_r / (2.0 * math.pi ** 2)})
+    return {"packing": packing, "Lx": Lx, "Ly": Ly, "Lz": Lz, "D0": D0, "nu": nu, "rows": rows}
+
+
+if __name__ == "__main__":  # pragma: no cover
+    # python -m paper_1105_3634_gb300.taylor [--packings 0.211 0.332] [--lx 40 80] [--pe 0.5 1 1.5 2]
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="Taylor dispersion of Sec. V (Figs. 3-5) on the GPU")
+    ap.add_argument("--packings", type=float, nargs="+", default=[0.211, 0.332])
+    ap.add_argument("--lx", type=int, nargs="+", default=[40, 80])
+    ap.add_argument("--pe", type=float, nargs="+", default=[0.5, 1.0, 1.5, 2.0])
+    args = ap.parse_args()
+    from . import mlb as _mlb
+    for packing in args.packings:
+        for Lx in args.lx:
+            print(json.dumps(paper_curve(_mlb, packing, Lx, args.pe)), flush=True)

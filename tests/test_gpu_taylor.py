@@ -39,3 +39,56 @@ def test_cosine_flow_taylor_dispersion(gpu):
     # the enhancement grows as Pe^2
     assert enh[0] < enh[1] < enh[2]
     assert 3.0 < enh[1] / enh[0] < 5.0
+
+
+def test_cosine_flow_d_eff_gpu_equals_oracle(gpu):
+    """The same Taylor experiment (cosine flow held by the body force, Eq.
+    ushape; concentration wave along x, Eq. perturba) measured on the GPU and
+    on the FP64 oracle with identical inputs: D(0) and D_eff at Pe ~ 2.5 agree
+    within 1 % (measured agreement is printed)."""
+    import oracle_sim
+    lat = W.Lattice(shape=(64, 16, 4), sigma=[1.0, 1.5], tau=1.0)
+    n0 = W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5])
+    nu = T.measure_viscosity(gpu, lat, n0)
+    orc = oracle_sim.module()
+    kw = dict(t0=100, t1=600, every=50)
+    out = {}
+    for U in (0.0, 0.04):
+        d_gpu, u_gpu = T.measure_dispersion(gpu, lat, n0, U, nu, **kw)
+        d_orc, u_orc = T.measure_dispersion(orc, lat, n0, U, nu, **kw)
+        out[U] = (d_gpu, d_orc)
+        print(f"U={U}: D_eff GPU {d_gpu:.6f} oracle {d_orc:.6f} (rel. {abs(d_gpu - d_orc) / d_orc:.1e}); "
+              f"flow {u_gpu:.5f} / {u_orc:.5f}")
+        assert abs(d_gpu - d_orc) < 0.01 * d_orc
+    assert out[0.04][0] > 1.05 * out[0.0][0]                     # the flow does enhance dispersion
+
+
+def test_three_species_channel_d_eff_gpu_equals_oracle(gpu):
+    """The Taylor channel of the workload at a reduced size, 64 x 16 x 8:
+    solvents sigma = 2, 2.5 at packing 0.211, a dilute solute sigma = 3
+    (mole fraction 1e-3), walls normal to y moving at -0.05 and +0.05.  The
+    solute's effective diffusion along x, measured on the GPU and on the FP64
+    oracle with identical inputs, agrees within 1 %."""
+    import oracle_sim
+    lat, n = W.taylor_channel((64, 16, 8), U=0.05)
+    n0 = [float(n[0].mean()), float(n[1].mean()), 1e-3 * float(n[0].mean() + n[1].mean())]
+    res = {}
+    for name, mod in (("gpu", gpu), ("oracle", oracle_sim.module())):
+        res[name] = T.measure_channel_dispersion(mod, lat, n0, species=2, t0=100, t1=500, every=50)
+    rel = abs(res["gpu"] - res["oracle"]) / res["oracle"]
+    print(f"channel solute D_eff: GPU {res['gpu']:.6f} oracle {res['oracle']:.6f} (rel. {rel:.1e})")
+    assert rel < 0.01
+
+
+def test_paper_fig3_mixture_taylor_dispersion(gpu):
+    """The experiment of Sec. V, Fig. 3: sigma_AA = 8, sigma_BB = 4 (762-point
+    contact shells), c_0 = 0.5, packing 0.211, an 80 x 40 x 40 box, cosine flow
+    at Pe = 1.  D_eff / D(0) equals the exact passive-scalar ratio for the flow
+    reached within 3 % and follows Eq. taylordiff."""
+    res = T.paper_curve(gpu, 0.211, 80, [1.0])
+    r = res["rows"][0]
+    print({k: (round(v, 5) if isinstance(v, float) else v) for k, v in res.items() if k != "rows"}, r)
+    assert res["D0"] > 0 and res["nu"] > 0
+    assert abs(r["Pe"] - 1.0) < 0.1
+    assert r["ratio"] > 1.0
+    assert abs(r["ratio"] - r["ratio_passive_scalar"]) < 0.03 * r["ratio_passive_scalar"]
