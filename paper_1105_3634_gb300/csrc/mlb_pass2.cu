@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const 
 }
 
 // ------------------------------------------------------------------ tiled variants
-template <int S, int R, bool DRAG, int TY>
+template <int S, int R, bool DRAG, int TY, int NSL = 2 * R + 2>
 __device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
                                                   const float4 *sf, const float *sg, int kz, int cidx,
                                                   const PairW<S> &w, const float (&us)[S][3], float (&acc)[S][3])
@@ -142,7 +142,7 @@ __device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const ml
             const float4 e0 = __ldg(&tab[2 * k]);
             const float4 e1 = __ldg(&tab[2 * k + 1]);
             const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
-            const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);
+            const int sp = ring(kz + dz, NSL), sm = ring(kz - dz, NSL);
             const float4 vp = sf[sp * S * T::PLANE + b * T::PLANE + cidx + off];
             const float4 vm = sf[sm * S * T::PLANE + b * T::PLANE + cidx - off];
             const float np = nr + vp.x, nm = nr + vm.x;
@@ -220,15 +220,15 @@ __device__ __forceinline__ void pass2_cube_class(const mlbi_params &p, const flo
     });
 }
 
-template <int S, bool DRAG>
+template <int S, bool DRAG, int NSL = 4>
 __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *sf, const float *sg, int kz, int cidx,
                                            const PairW<S> &w, const float (&us)[S][3], float (&acc)[S][3])
 {
     using T = Tile<S, 1>;
-    const int f[3] = {ring(kz - 1, T::NSLOT) * S * T::PLANE + cidx, ring(kz, T::NSLOT) * S * T::PLANE + cidx,
-                      ring(kz + 1, T::NSLOT) * S * T::PLANE + cidx};
-    const int g[3] = {ring(kz - 1, T::NSLOT) * T::NP * T::PLANE + cidx, ring(kz, T::NSLOT) * T::NP * T::PLANE + cidx,
-                      ring(kz + 1, T::NSLOT) * T::NP * T::PLANE + cidx};
+    const int f[3] = {ring(kz - 1, NSL) * S * T::PLANE + cidx, ring(kz, NSL) * S * T::PLANE + cidx,
+                      ring(kz + 1, NSL) * S * T::PLANE + cidx};
+    const int g[3] = {ring(kz - 1, NSL) * T::NP * T::PLANE + cidx, ring(kz, NSL) * T::NP * T::PLANE + cidx,
+                      ring(kz + 1, NSL) * T::NP * T::PLANE + cidx};
 #pragma unroll
     for (int b = 0; b < S; ++b) {
         pass2_cube_class<S, DRAG, 0>(p, sf, sg, b, f, g, w, us, acc);
@@ -239,12 +239,12 @@ __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *s
 
 // the shell sums of the acceleration of the site at ring position kz of the
 // tile (centre slot cs), added to acc
-template <int S, int R, bool DRAG, int TY>
+template <int S, int R, bool DRAG, int TY, int NSL = 2 * R + 2>
 __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *__restrict__ tab, const float4 *sf,
                                            const float *sg, int kz, int cidx, float (&acc)[S][3])
 {
     using T = Tile<S, R, TY>;
-    const int cs = ring(kz, T::NSLOT);
+    const int cs = ring(kz, NSL);
     float dgc[T::NP];
 #pragma unroll
     for (int q = 0; q < T::NP; ++q) dgc[q] = sg[cs * T::NP * T::PLANE + q * T::PLANE + cidx];
@@ -256,8 +256,8 @@ __device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entr
         const float4 v = sf[cs * S * T::PLANE + a * T::PLANE + cidx];
         us[a][0] = v.y; us[a][1] = v.z; us[a][2] = v.w;
     }
-    if constexpr (R == 1 && TY == kBY) pass2_cube<S, DRAG>(p, sf, sg, kz, cidx, w, us, acc);
-    else pass2_tile_shells<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, w, us, acc);
+    if constexpr (R == 1 && TY == kBY) pass2_cube<S, DRAG, NSL>(p, sf, sg, kz, cidx, w, us, acc);
+    else pass2_tile_shells<S, R, DRAG, TY, NSL>(p, tab, sf, sg, kz, cidx, w, us, acc);
 }
 
 template <int S, int R, bool DRAG, int TY>
@@ -425,13 +425,20 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2) k_pass2_collide(con
 // collision, so they land while the plane's shell sums run.  Shared layouts
 // are those of the cp.async variant: population (a, i) of thread t at
 // sF[(a * 19 + i) * 128 + t], moments and rest force at sM / sR[a * 128 + t].
+// The stencil ring holds 2R + 1 planes only: the next plane is staged into
+// the slot of plane z - R once every thread has finished plane z's shell
+// sums (a second barrier per plane), and lands during the collisions.  The
+// 9 KB this saves (R = 1, S = 2) and a 128-register bound give 4 resident
+// blocks per SM instead of 3.
 template <int S, int R>
 struct TmaTile {
     using T = Tile<S, R>;
+    static constexpr int NSL = 2 * R + 1;
     static constexpr size_t pad(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t ring_bytes = (size_t)NSL * T::PLANE * (S * sizeof(float4) + T::NP * sizeof(float));
     static constexpr uint32_t pops_bytes = (uint32_t)S * MLBI_Q * T::NT * 4;
     static constexpr uint32_t v4_bytes = (uint32_t)S * T::NT * 16;
-    static constexpr size_t pops_off = pad(T::bytes);
+    static constexpr size_t pops_off = pad(ring_bytes);
     static constexpr size_t mom_off = pops_off + pops_bytes;
     static constexpr size_t rest_off = mom_off + v4_bytes;
     static constexpr size_t bytes = rest_off + v4_bytes + 128;       // + alignment slack of the base
@@ -439,7 +446,7 @@ struct TmaTile {
 };
 
 template <int S, int R, bool DRAG>
-__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2)
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
     k_pass2_collide_tma(const mlbi_params p, const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
                         const float4 *__restrict__ pst, float *__restrict__ fout, unsigned int *__restrict__ flags,
                         const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_mom,
@@ -451,8 +458,9 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2)
     __shared__ __align__(8) uint64_t bar_mem;
     // the bulk copies want 128-byte aligned destinations
     char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    constexpr int NSL = F::NSL;
     float4 *sf = reinterpret_cast<float4 *>(base);
-    float *sg = reinterpret_cast<float *>(sf + (size_t)T::NSLOT * S * T::PLANE);
+    float *sg = reinterpret_cast<float *>(sf + (size_t)NSL * S * T::PLANE);
     float *sF = reinterpret_cast<float *>(base + F::pops_off);
     float4 *sM = reinterpret_cast<float4 *>(base + F::mom_off);
     float4 *sR = reinterpret_cast<float4 *>(base + F::rest_off);
@@ -477,7 +485,7 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2)
     }
     int xy[T::J];
     stage_sites<S, R>(p, x0, y0, xy);
-    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, T::NSLOT), pst, dg, sf, sg);
+    for (int k = 0; k < 2 * R + 1; ++k) stage_plane<S, R>(p, xy, z0 - R + k, ring(k, NSL), pst, dg, sf, sg);
     cp_async_commit();
     __syncthreads();                                            // the barrier is initialised
     if (tid == 0) issue(z0);
@@ -488,11 +496,12 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 3 : 2)
         if (s_fail) break;            // uniform: read after the barrier
         if (tid == 0 && z > z0) issue(z);
         const int kz = z - z0 + R;
-        if (z + 1 < z1) stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, T::NSLOT), pst, dg, sf, sg);
-        cp_async_commit();
         float acc[S][3];
         zero_acc<S>(acc);
-        if (active) pass2_site<S, R, DRAG, kBY>(p, tab, sf, sg, kz, cidx, acc);
+        if (active) pass2_site<S, R, DRAG, kBY, NSL>(p, tab, sf, sg, kz, cidx, acc);
+        __syncthreads();              // every thread is done with plane z - R: its slot takes plane z + R + 1
+        if (z + 1 < z1) stage_plane<S, R>(p, xy, z + R + 1, ring(kz + R + 1, NSL), pst, dg, sf, sg);
+        cp_async_commit();
         // each thread waits for the copies itself, so warps move on to their
         // collisions independently; a wait that gives up marks the block failed,
         // and every thread leaves at the next barrier
