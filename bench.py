@@ -685,11 +685,24 @@ def run_variants(mlb, torch, plain_value, plain_ms):
     e1.record(bstream)
     batch.synchronize()
     ms = e0.elapsed_time(e1) / 10
+    grouped = batch.grouped_members()
+    batch.close()
+    # the same members, each by its own launches inside the graph
+    batch = mlb.Batch(sims, stream=bstream, lanes=0)
+    batch.step(2)
+    batch.synchronize()
+    e0.record(bstream)
+    batch.step(10)
+    e1.record(bstream)
+    batch.synchronize()
+    ms_own = e0.elapsed_time(e1) / 10
     batch.close()
     for sim in sims:
         sim.close()
     out["ensemble_64"] = {"ms_per_ensemble_step": ms, "value": units / ms / 1e3, "ratio_to_plain": units / ms / 1e3 / plain_value,
-                          "species_sites": units, "D_mutual_rel_error": 0.0,
+                          "species_sites": units, "grouped_members": grouped,
+                          "ms_per_ensemble_step_own_launches": ms_own, "grouping_speedup": ms_own / ms,
+                          "D_mutual_rel_error": 0.0,
                           "note": "every member's populations equal those of the member stepped alone bit for bit"}
     return out
 
@@ -785,6 +798,17 @@ def run_ensemble(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = reduce_max(e0.elapsed_time(e1), dist, dev)
+    grouped = batch.grouped_members()
+    # (c) the same batch with every member by its own launches
+    own = mlb.Batch(sims, stream=bstream, lanes=0)
+    own.step(warm)
+    own.synchronize()
+    e0.record(bstream)
+    own.step(steps)
+    e1.record(bstream)
+    own.synchronize()
+    ms_own = reduce_max(e0.elapsed_time(e1), dist, dev)
+    own.close()
     value = units * steps * world / (ms * 1e-3) / 1e6
     seq_value = units * steps * world / t_seq / 1e6
     peak, peak_kind = measured_peak_hbm()
@@ -803,6 +827,9 @@ def run_ensemble(args, rank, world, local_rank):
                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                         "note": f"{design_bytes} B per species-site: the three step kernels' algorithmic bytes"},
            "ensemble": {"sequential_value": seq_value, "speedup_vs_sequential": value / seq_value,
+                        "grouped_members": grouped,
+                        "own_launches_value": units * steps * world / (ms_own * 1e-3) / 1e6,
+                        "grouping_speedup": ms_own / ms,
                         "batch_wall_value": units * steps * world / t_batch_wall / 1e6,
                         "autotuned_zchunks": zs,
                         "fused_members": sum(1 for _, f in tuned if f)},

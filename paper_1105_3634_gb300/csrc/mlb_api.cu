@@ -643,6 +643,14 @@ mlbi_buffers pass2_buffers(const mlb_ctx *c)
     return b;
 }
 
+// the column attraction of the moments into b.attr (p.attr_r > 0)
+mlb_status attraction(mlb_ctx *c)
+{
+    if (use_tc_attraction(c)) MLB_CUDA(c, mlbi_launch_attraction_tc(c->p, c->b, c->tc, c->stream));
+    else MLB_CUDA(c, mlbi_launch_attraction(c->p, c->b, c->stream));
+    return MLB_OK;
+}
+
 mlb_status forces_pass1(mlb_ctx *c, bool sums)
 {
     if (c->p.local_g) {
@@ -654,8 +662,8 @@ mlb_status forces_pass1(mlb_ctx *c, bool sums)
     }
     if (c->p.attr_r) {
         Timed t(c, K_ATTRACTION);
-        if (use_tc_attraction(c)) MLB_CUDA(c, mlbi_launch_attraction_tc(c->p, c->b, c->tc, c->stream));
-        else MLB_CUDA(c, mlbi_launch_attraction(c->p, c->b, c->stream));
+        const mlb_status st = attraction(c);
+        if (st != MLB_OK) return st;
     }
     if (c->surr && c->surr_active) {
         // the network's F^hc into attr; every surr_every steps the exact pass 1
@@ -1342,6 +1350,15 @@ struct mlb_batch {
     std::vector<int> cur;                     // members' buffer parity at the capture
     cudaEvent_t cap_fork = nullptr, join = nullptr;
     std::vector<cudaEvent_t> cap_done, pre;   // per member: capture join, order before a launch
+    // grouped launches: members that take the same grouped kernels step by one
+    // launch per stage (mlbi_group); the others by their own launches
+    int lanes = 1;                            // 0: no grouping; else lanes per group
+    long long group_max_sites = 1ll << 17;    // larger members step by their own launches
+    std::vector<mlbi_group> groups;           // one per lane
+    std::vector<std::vector<int>> group_members;
+    void *gmem = nullptr;                     // device: member tables and block tables of every lane
+    std::vector<cudaEvent_t> lane_ev;         // per lane: lane done
+    cudaEvent_t attr_fork = nullptr;
     bool failed = false;
     std::string err;
 };
@@ -1360,8 +1377,136 @@ mlb_status batch_fail(mlb_batch *b, mlb_status s, const char *fmt, ...)
     return s;
 }
 
-// Capture two steps of every member into a graph: fork from the batch stream
-// onto each member's stream, two (forces, advance) pairs per member, join back.
+// whether a member can step inside a grouped launch (the fused pass 2 +
+// collision is bitwise the split pair, so a tuned split does not exclude it)
+bool groupable(const mlb_batch *b, const mlb_ctx *c)
+{
+    return c->p.N <= b->group_max_sites && c->sweeps == 1 && !(c->surr && c->surr_active) &&
+           !(c->desc.flags & MLB_SPLIT_COLLIDE) && mlbi_group_supported(c->p, c->b);
+}
+
+void free_groups(mlb_batch *b)
+{
+    if (b->gmem) {
+        cudaStreamSynchronize(b->stream);     // a graph still in flight may read the tables
+        cudaFree(b->gmem);
+        b->gmem = nullptr;
+    }
+    b->groups.clear();
+    b->group_members.clear();
+}
+
+// Partition the members by (species, shell reach, drag mode) among those that
+// can be grouped, and each such group into `lanes` lanes (members dealt in
+// order of size, so the lanes carry similar work); write each lane's member
+// table and per-stage block tables (larger members first) to one device
+// allocation.
+mlb_status build_groups(mlb_batch *b)
+{
+    free_groups(b);
+    if (b->lanes < 1) return MLB_OK;
+    std::vector<std::vector<int>> sets;
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        const mlb_ctx *c = b->m[i];
+        if (!groupable(b, c)) continue;
+        bool placed = false;
+        for (auto &g : sets) {
+            const mlbi_params &q = b->m[g[0]]->p;
+            if (q.S == c->p.S && q.tile_r == c->p.tile_r && q.drag_only == c->p.drag_only) {
+                g.push_back((int)i);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) sets.push_back({(int)i});
+    }
+    for (auto &g : sets) {
+        if (g.size() < 2) continue;           // one member steps as fast by its own launches
+        std::stable_sort(g.begin(), g.end(), [&](int x, int y) { return b->m[x]->p.N > b->m[y]->p.N; });
+        const size_t nl = std::min(g.size(), (size_t)b->lanes);
+        std::vector<std::vector<int>> lanes(nl);
+        for (size_t k = 0; k < g.size(); ++k) lanes[k % nl].push_back(g[k]);
+        for (auto &l : lanes) b->group_members.push_back(l);
+    }
+    while (b->lane_ev.size() < b->group_members.size()) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return batch_fail(b, MLB_ECUDA, "cudaEventCreate failed");
+        b->lane_ev.push_back(ev);
+    }
+    if (b->group_members.empty()) return MLB_OK;
+    // layout: per group the members, then the three block tables
+    std::vector<size_t> off_mem, off_blk[3];
+    std::vector<std::vector<int4>> tables[3];
+    size_t bytes = 0;
+    auto take = [&](size_t n) { bytes = (bytes + 255) & ~size_t(255); const size_t o = bytes; bytes += n; return o; };
+    for (const auto &g : b->group_members) {
+        off_mem.push_back(take(g.size() * sizeof(mlbi_member)));
+        for (int k = 0; k < 3; ++k) {
+            std::vector<int4> t;
+            for (size_t j = 0; j < g.size(); ++j) {
+                int grid[3];
+                mlbi_group_grid(b->m[g[j]]->p, k, grid);
+                const long long nb = (long long)grid[0] * grid[1] * grid[2];
+                if (nb + (long long)t.size() > (1ll << 30)) return batch_fail(b, MLB_EINVAL, "group too large");
+                for (long long q = 0; q < nb; ++q) {
+                    if (k == MLBI_GROUP_MOMENTS)
+                        t.push_back(make_int4((int)j, (int)q, (int)nb, 0));
+                    else
+                        t.push_back(make_int4((int)j, (int)(q % grid[0]), (int)(q / grid[0] % grid[1]),
+                                              (int)(q / ((long long)grid[0] * grid[1]))));
+                }
+            }
+            off_blk[k].push_back(take(t.size() * sizeof(int4)));
+            tables[k].push_back(std::move(t));
+        }
+    }
+    cudaError_t e = cudaMalloc(&b->gmem, bytes);
+    if (e != cudaSuccess) {
+        b->gmem = nullptr;
+        return batch_fail(b, MLB_ENOMEM, "group tables: %s", cudaGetErrorString(e));
+    }
+    char *base = static_cast<char *>(b->gmem);
+    for (size_t gi = 0; gi < b->group_members.size() && e == cudaSuccess; ++gi) {
+        const auto &g = b->group_members[gi];
+        std::vector<mlbi_member> mem(g.size());
+        for (size_t j = 0; j < g.size(); ++j) {
+            const mlb_ctx *c = b->m[g[j]];
+            std::memset(static_cast<void *>(&mem[j]), 0, sizeof(mlbi_member));
+            mem[j].map_f[0] = c->maps.f[0];
+            mem[j].map_f[1] = c->maps.f[1];
+            mem[j].map_mom = c->maps.mom;
+            mem[j].map_frest = c->maps.frest;
+            mem[j].p = c->p;
+            mem[j].b = c->b;
+            mem[j].b.maps = nullptr;
+            mem[j].cur = c->cur;
+        }
+        e = cudaMemcpy(base + off_mem[gi], mem.data(), mem.size() * sizeof(mlbi_member), cudaMemcpyHostToDevice);
+        mlbi_group grp{};
+        grp.mem = reinterpret_cast<const mlbi_member *>(base + off_mem[gi]);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            e = cudaMemcpy(base + off_blk[k][gi], tables[k][gi].data(), tables[k][gi].size() * sizeof(int4),
+                           cudaMemcpyHostToDevice);
+            grp.blk[k] = reinterpret_cast<const int4 *>(base + off_blk[k][gi]);
+            grp.nblk[k] = (int)tables[k][gi].size();
+        }
+        const mlbi_params &q = b->m[g[0]]->p;
+        grp.S = q.S;
+        grp.R = q.tile_r;
+        grp.drag = q.drag_only;
+        b->groups.push_back(grp);
+    }
+    if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "group tables: %s", cudaGetErrorString(e));
+    return MLB_OK;
+}
+
+// Capture two steps of every member into a graph.  Grouped members: per step
+// one launch per stage for each lane on the lane's stream (forked from the
+// batch stream), the column attractions of members that have one forked onto
+// their own streams between the moments and pass 1.  The other members: fork
+// from the batch stream onto each member's stream, two (forces, advance)
+// pairs per member, join back.
 mlb_status batch_capture(mlb_batch *b)
 {
     if (b->exec) {
@@ -1371,11 +1516,44 @@ mlb_status batch_capture(mlb_batch *b)
     for (size_t i = 0; i < b->m.size(); ++i)
         if (b->m[i]->surr && b->m[i]->surr_active)
             return batch_fail(b, MLB_EINVAL, "member %zu uses a surrogate (its rechecks read back to the host)", i);
+    mlb_status st = build_groups(b);
+    if (st != MLB_OK) return st;
+    std::vector<char> in_group(b->m.size(), 0);
+    for (const auto &g : b->group_members)
+        for (int i : g) in_group[i] = 1;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
-    mlb_status st = MLB_OK;
     e = cudaEventRecord(b->cap_fork, b->stream);
+    // each lane on the stream of its first member
+    for (size_t l = 0; l < b->groups.size() && e == cudaSuccess && st == MLB_OK; ++l) {
+        const mlbi_group &g = b->groups[l];
+        cudaStream_t ls = b->m[b->group_members[l][0]]->stream;
+        e = cudaStreamWaitEvent(ls, b->cap_fork, 0);
+        for (int odd = 0; odd < 2 && e == cudaSuccess && st == MLB_OK; ++odd) {
+            e = mlbi_launch_group_moments(g, odd, ls);
+            bool forked = false;
+            for (int i : b->group_members[l]) {
+                mlb_ctx *c = b->m[i];
+                if (!c->p.attr_r || e != cudaSuccess || st != MLB_OK) continue;
+                if (c->stream == ls) {
+                    st = attraction(c);
+                    continue;
+                }
+                if (!forked) e = cudaEventRecord(b->attr_fork, ls);
+                forked = true;
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, b->attr_fork, 0);
+                if (e == cudaSuccess) st = attraction(c);
+                if (e == cudaSuccess && st == MLB_OK) e = cudaEventRecord(b->cap_done[i], c->stream);
+                if (e == cudaSuccess && st == MLB_OK) e = cudaStreamWaitEvent(ls, b->cap_done[i], 0);
+            }
+            if (e == cudaSuccess && st == MLB_OK) e = mlbi_launch_group_pass1(g, ls);
+            if (e == cudaSuccess && st == MLB_OK) e = mlbi_launch_group_pass2_collide(g, odd, ls);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->lane_ev[l], ls);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->lane_ev[l], 0);
+    }
     for (size_t i = 0; i < b->m.size() && e == cudaSuccess && st == MLB_OK; ++i) {
+        if (in_group[i]) continue;
         mlb_ctx *c = b->m[i];
         const bool prof = c->profiling;
         c->profiling = false;
@@ -1394,6 +1572,7 @@ mlb_status batch_capture(mlb_batch *b)
     if (e == cudaSuccess) e = ee;
     if (st != MLB_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
+        free_groups(b);
         if (st != MLB_OK) return batch_fail(b, MLB_ECUDA, "capture: member launch failed");
         return batch_fail(b, MLB_ECUDA, "capture: %s", cudaGetErrorString(e));
     }
@@ -1441,6 +1620,7 @@ mlb_status mlb_batch_create(mlb_ctx *const *members, int32_t n, void *stream, ml
     const unsigned fl = cudaEventDisableTiming;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cap_fork, fl);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, fl);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->attr_fork, fl);
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&b->cap_done[i], fl);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->pre[i], fl);
@@ -1504,6 +1684,32 @@ mlb_status mlb_batch_synchronize(mlb_batch *b)
     return MLB_OK;
 }
 
+mlb_status mlb_batch_set_grouping(mlb_batch *b, int32_t lanes, int64_t max_sites)
+{
+    if (!b) return MLB_EINVAL;
+    if (b->failed) return MLB_ESTATE;
+    if (lanes < 0 || lanes > 64) return batch_fail(b, MLB_EINVAL, "lanes must be 0..64");
+    if (max_sites < 1) return batch_fail(b, MLB_EINVAL, "max_sites must be >= 1");
+    if (b->lanes != lanes || b->group_max_sites != max_sites) {
+        b->lanes = lanes;
+        b->group_max_sites = max_sites;
+        if (b->exec) {
+            cudaStreamSynchronize(b->stream);
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    return MLB_OK;
+}
+
+int32_t mlb_batch_grouped_members(const mlb_batch *b)
+{
+    if (!b) return 0;
+    int32_t n = 0;
+    for (const auto &g : b->group_members) n += (int32_t)g.size();
+    return n;
+}
+
 const char *mlb_batch_last_error(const mlb_batch *b)
 {
     return b ? b->err.c_str() : "null batch";
@@ -1514,6 +1720,10 @@ void mlb_batch_destroy(mlb_batch *b)
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    free_groups(b);
+    for (cudaEvent_t e : b->lane_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->attr_fork) cudaEventDestroy(b->attr_fork);
     if (b->cap_fork) cudaEventDestroy(b->cap_fork);
     if (b->join) cudaEventDestroy(b->join);
     for (cudaEvent_t e : b->cap_done)

@@ -185,6 +185,26 @@ __device__ __forceinline__ void load_centre(const mlbi_params &p, const float4 *
     }
 }
 
+// ------------------------------------------------------------------ grouped launches
+// The block's member parameters, copied from global into shared memory by the
+// whole block (ends with a barrier).
+__device__ __forceinline__ void group_params(const mlbi_member *__restrict__ m, mlbi_params &sp)
+{
+    static_assert(sizeof(mlbi_params) % 4 == 0, "parameters copied as words");
+    const int *src = reinterpret_cast<const int *>(&m->p);
+    int *dst = reinterpret_cast<int *>(&sp);
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = tid; k < (int)(sizeof(mlbi_params) / 4); k += nt) dst[k] = __ldg(src + k);
+    __syncthreads();
+}
+
+// make a tensor map that the host wrote to global memory visible to the bulk
+// copies of this thread (the tensormap proxy's acquire of its 128 bytes)
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 inline dim3 tiled_grid(const mlbi_params &p)
 {
     return dim3((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + kBY - 1) / kBY), (unsigned)p.nz);

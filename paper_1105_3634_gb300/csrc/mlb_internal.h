@@ -198,6 +198,37 @@ cudaError_t mlbi_launch_import_fext(const mlbi_params &p, const mlbi_buffers &b,
 // float4 [S][N] (x, y, z) -> FP64 [S][3][N]
 cudaError_t mlbi_launch_export_vec(const mlbi_params &p, const float4 *src, double *dst, cudaStream_t s);
 
+// ------------------------------------------------------------------ grouped launches
+// One launch of a stage steps every member of a group of independent
+// lattices (mlb_batch): the members take the same kernel instantiation (same
+// S, shell reach and drag mode; site-local contact values; the fused pass 2 +
+// collision on bulk tensor copies), each block reads its member and tile from
+// a block table, copies the member's parameters into shared memory and runs
+// the stage's per-block code unchanged, so a member's arithmetic is bitwise
+// that of its own launches.  Device memory; the tensor maps are the
+// members' host-encoded descriptors copied to global memory.
+struct mlbi_member {
+    CUtensorMap map_f[2];            // populations f[0], f[1]
+    CUtensorMap map_mom, map_frest;
+    mlbi_params p;
+    mlbi_buffers b;                  // device pointers of the member (b.maps unused)
+    int cur;                         // the buffer f[cur] the member reads at the group's even steps
+};
+struct mlbi_group {
+    const mlbi_member *mem;          // [nmem] device
+    const int4 *blk[3];              // per stage: [nblk] {member, block x, block y, block z} device
+    int nblk[3];                     // (moments: {member, block, blocks of the member, 0})
+    int S, R, drag;                  // the shared instantiation: species, shell reach (1, 2), drag only
+};
+enum { MLBI_GROUP_MOMENTS = 0, MLBI_GROUP_PASS1 = 1, MLBI_GROUP_PASS2 = 2 };
+// whether a member can join a group, and its stage grids (blocks per stage)
+bool mlbi_group_supported(const mlbi_params &p, const mlbi_buffers &b);
+void mlbi_group_grid(const mlbi_params &p, int stage, int grid[3]);
+// odd: the group's odd step (members read f[cur ^ 1])
+cudaError_t mlbi_launch_group_moments(const mlbi_group &g, int odd, cudaStream_t s);
+cudaError_t mlbi_launch_group_pass1(const mlbi_group &g, cudaStream_t s);
+cudaError_t mlbi_launch_group_pass2_collide(const mlbi_group &g, int odd, cudaStream_t s);
+
 // learned surrogate of the hard-core force (mlb_surrogate.cu)
 struct mlb_net;
 bool mlbi_net_matches(const mlb_net *n, int nx, int ny, int nz);

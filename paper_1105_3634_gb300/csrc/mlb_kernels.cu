@@ -138,16 +138,17 @@ __global__ void __launch_bounds__(kBX * kBY) k_gfield(mlbi_params p, const float
 // ------------------------------------------------------------------ moments with local contact values
 // When every smoothing ball is the single site (kappa sigma < 1), g_ab at r
 // depends on the moments at r only: one pass over f gives both.
+// the sites of block `blk` of `nblk` (grid-stride)
 template <int S, bool SUMS>
-__global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const float *__restrict__ f,
-                                                      float4 *__restrict__ mom, float *__restrict__ dg,
-                                                      unsigned int *__restrict__ flags, double *__restrict__ partial)
+__device__ __forceinline__ void moments_g_blocks(const mlbi_params &p, const float *__restrict__ f,
+                                                 float4 *__restrict__ mom, float *__restrict__ dg,
+                                                 unsigned int *__restrict__ flags, double *__restrict__ partial,
+                                                 long long blk, long long nblk)
 {
     constexpr int NP = S * (S + 1) / 2;
     const long long N = p.N;
     ConsSums<S> cs;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
-         r += (long long)gridDim.x * blockDim.x) {
+    for (long long r = blk * blockDim.x + threadIdx.x; r < N; r += nblk * blockDim.x) {
         float dn[S], u[S][3], j[S][3], dgv[NP];
         site_moments<S>(p, GlobalPops{f + r, N}, dn, u, j);
 #pragma unroll
@@ -158,6 +159,27 @@ __global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const
         if constexpr (SUMS) cs.add(dn, u, j);
     }
     if constexpr (SUMS) cs.store(partial, flags);
+}
+
+template <int S, bool SUMS>
+__global__ void __launch_bounds__(kBlock) k_moments_g(const mlbi_params p, const float *__restrict__ f,
+                                                      float4 *__restrict__ mom, float *__restrict__ dg,
+                                                      unsigned int *__restrict__ flags, double *__restrict__ partial)
+{
+    moments_g_blocks<S, SUMS>(p, f, mom, dg, flags, partial, blockIdx.x, gridDim.x);
+}
+
+// every member of a group: block table entries {member, block, blocks of the member, 0}
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_moments_g_group(const mlbi_member *__restrict__ mem,
+                                                            const int4 *__restrict__ blk, int odd)
+{
+    __shared__ mlbi_params sp;
+    const int4 e = blk[blockIdx.x];
+    const mlbi_member *m = mem + e.x;
+    group_params(m, sp);
+    const mlbi_buffers &b = m->b;
+    moments_g_blocks<S, false>(sp, b.f[m->cur ^ odd], b.mom, b.dg, b.flags, nullptr, e.y, e.z);
 }
 
 template <int S>
@@ -340,6 +362,21 @@ cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, i
     }
     MLBI_DISPATCH_S((k_moments_g<SS, false><<<grid_for(p.N), kBlock, 0, s>>>(p, b.f[cur], b.mom, b.dg, b.flags,
                                                                              nullptr)));
+    return cudaGetLastError();
+}
+
+cudaError_t mlbi_launch_group_moments(const mlbi_group &g, int odd, cudaStream_t s)
+{
+    if (g.nblk[MLBI_GROUP_MOMENTS] < 1) return cudaErrorInvalidValue;
+    const unsigned nb = (unsigned)g.nblk[MLBI_GROUP_MOMENTS];
+    const int4 *blk = g.blk[MLBI_GROUP_MOMENTS];
+    switch (g.S) {
+    case 1: k_moments_g_group<1><<<nb, kBlock, 0, s>>>(g.mem, blk, odd); break;
+    case 2: k_moments_g_group<2><<<nb, kBlock, 0, s>>>(g.mem, blk, odd); break;
+    case 3: k_moments_g_group<3><<<nb, kBlock, 0, s>>>(g.mem, blk, odd); break;
+    case 4: k_moments_g_group<4><<<nb, kBlock, 0, s>>>(g.mem, blk, odd); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

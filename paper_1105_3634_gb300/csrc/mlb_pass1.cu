@@ -41,7 +41,37 @@ cudaError_t launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream
     return cudaGetLastError();
 }
 
+template <int S, int R, bool DRAG>
+cudaError_t launch_pass1_group(const mlbi_group &g, cudaStream_t s)
+{
+    constexpr int TY = mlbi_tile_ty(S, R);
+    if constexpr (TY == 0) {
+        return cudaErrorInvalidValue;
+    } else {
+        using T = Tile<S, R, TY>;
+        auto k = k_pass1_group<S, R, DRAG, TY>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)g.nblk[MLBI_GROUP_PASS1], dim3(kBX, TY), T::bytes, s>>>(g.mem, g.blk[MLBI_GROUP_PASS1]);
+        return cudaGetLastError();
+    }
+}
+
+template <int S, int R>
+cudaError_t launch_pass1_group_r(const mlbi_group &g, cudaStream_t s)
+{
+    return g.drag ? launch_pass1_group<S, R, true>(g, s) : launch_pass1_group<S, R, false>(g, s);
+}
+
 }  // namespace
+
+cudaError_t mlbi_launch_group_pass1(const mlbi_group &g, cudaStream_t s)
+{
+    if (g.nblk[MLBI_GROUP_PASS1] < 1) return cudaErrorInvalidValue;
+    if (g.S == 1) return g.R == 1 ? launch_pass1_group_r<1, 1>(g, s) : launch_pass1_group_r<1, 2>(g, s);
+    if (g.S == 2) return g.R == 1 ? launch_pass1_group_r<2, 1>(g, s) : launch_pass1_group_r<2, 2>(g, s);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t mlbi_launch_pass1(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s)
 {

@@ -383,18 +383,20 @@ __device__ __forceinline__ void pass1_cube(const mlbi_params &p, const float4 *s
 // MODE: kExact; kSurrogate (no hard-core sums, attr holds F^hc); kSweep (mom
 // is the previous sweep's (n - n_ref, u*) field, mom_c the moments, frest is
 // read, pst receives the sweep's u*)
+// the tile (bx, by, bz) of the tiled pass 1
 template <int S, int R, bool DRAG, int TY, int MODE>
-__global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S <= 2 ? (MODE == kSweep ? 4 : 6) : 2))
-    k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom, const float *__restrict__ dg,
-                  const mlbi_entry *__restrict__ tab, const float4 *__restrict__ fext, const float4 *__restrict__ attr,
-                  const float4 *__restrict__ mom_c, float4 *__restrict__ frest, float4 *__restrict__ pst)
+__device__ __forceinline__ void pass1_tile(const mlbi_params &p, const float4 *__restrict__ mom,
+                                           const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
+                                           const float4 *__restrict__ fext, const float4 *__restrict__ attr,
+                                           const float4 *__restrict__ mom_c, float4 *__restrict__ frest,
+                                           float4 *__restrict__ pst, int bx, int by, int bz)
 {
     constexpr bool HC = MODE == kExact;
     using T = Tile<S, R, TY>;
     extern __shared__ float4 smem[];
     float4 *sf = smem;                                                      // [NSLOT][S][PLANE]
     float *sg = reinterpret_cast<float *>(smem + (size_t)T::NSLOT * S * T::PLANE);   // [NSLOT][NP][PLANE]
-    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * TY, z0 = blockIdx.z * p.zchunk;
+    const int x0 = bx * kBX, y0 = by * TY, z0 = bz * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active = x < p.nx && y < p.ny;
@@ -450,6 +452,30 @@ __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S
         }
         pass1_finish<S, DRAG>(p, r, c, A, fext, frest, pst);
     }
+}
+
+template <int S, int R, bool DRAG, int TY, int MODE>
+__global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S <= 2 ? (MODE == kSweep ? 4 : 6) : 2))
+    k_pass1_tiled(const mlbi_params p, const float4 *__restrict__ mom, const float *__restrict__ dg,
+                  const mlbi_entry *__restrict__ tab, const float4 *__restrict__ fext, const float4 *__restrict__ attr,
+                  const float4 *__restrict__ mom_c, float4 *__restrict__ frest, float4 *__restrict__ pst)
+{
+    pass1_tile<S, R, DRAG, TY, MODE>(p, mom, dg, tab, fext, attr, mom_c, frest, pst, blockIdx.x, blockIdx.y,
+                                     blockIdx.z);
+}
+
+// every member of a group (block table entries {member, bx, by, bz}), the exact pass
+template <int S, int R, bool DRAG, int TY>
+__global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes + sizeof(mlbi_params), S <= 2 ? 6 : 2))
+    k_pass1_group(const mlbi_member *__restrict__ mem, const int4 *__restrict__ blk)
+{
+    __shared__ mlbi_params sp;
+    const int4 e = blk[blockIdx.x];
+    const mlbi_member *m = mem + e.x;
+    group_params(m, sp);
+    const mlbi_buffers &b = m->b;
+    pass1_tile<S, R, DRAG, TY, kExact>(sp, b.mom, b.dg, b.table, b.fext, b.attr, b.mom, b.frest, b.pst, e.y, e.z,
+                                       e.w);
 }
 
 }  // namespace

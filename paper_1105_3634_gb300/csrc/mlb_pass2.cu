@@ -445,12 +445,15 @@ struct TmaTile {
     static constexpr uint32_t tx_bytes = pops_bytes + 2 * v4_bytes;
 };
 
+// the tile (bx, by, bz) of the fused pass; the maps are kernel parameters or
+// (grouped launches) global-memory copies the issuing thread has acquired
 template <int S, int R, bool DRAG>
-__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
-    k_pass2_collide_tma(const mlbi_params p, const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
-                        const float4 *__restrict__ pst, float *__restrict__ fout, unsigned int *__restrict__ flags,
-                        const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_mom,
-                        const __grid_constant__ CUtensorMap map_rest)
+__device__ __forceinline__ void pass2_collide_tma_tile(const mlbi_params &p, const float *__restrict__ dg,
+                                                       const mlbi_entry *__restrict__ tab,
+                                                       const float4 *__restrict__ pst, float *__restrict__ fout,
+                                                       unsigned int *__restrict__ flags, const CUtensorMap *map_f,
+                                                       const CUtensorMap *map_mom, const CUtensorMap *map_rest,
+                                                       int bx, int by, int bz)
 {
     using T = Tile<S, R>;
     using F = TmaTile<S, R>;
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
     float4 *sR = reinterpret_cast<float4 *>(base + F::rest_off);
     __shared__ int s_fail;                                       // a wait gave up (read after a barrier)
     const uint32_t bar = smem_u32(&bar_mem);
-    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * p.zchunk;
+    const int x0 = bx * kBX, y0 = by * kBY, z0 = bz * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int tid = threadIdx.y * kBX + threadIdx.x;
@@ -475,9 +478,9 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
     const int sxy = x + p.nx * y, nxy = p.nx * p.ny;
     auto issue = [&](int z) {
         mbar_expect_tx(bar, F::tx_bytes);
-        tma_load_4d(smem_u32(sF), &map_f, bar, x0, y0, z, 0);
-        tma_load_5d(smem_u32(sM), &map_mom, bar, 0, x0, y0, z, 0);
-        tma_load_5d(smem_u32(sR), &map_rest, bar, 0, x0, y0, z, 0);
+        tma_load_4d(smem_u32(sF), map_f, bar, x0, y0, z, 0);
+        tma_load_5d(smem_u32(sM), map_mom, bar, 0, x0, y0, z, 0);
+        tma_load_5d(smem_u32(sR), map_rest, bar, 0, x0, y0, z, 0);
     };
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -527,6 +530,38 @@ __global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
     }
     cp_async_wait_all();
     if (s_fail && tid == 0) mbar_wait(bar, phase ^ 1u);       // one more bounded wait for the copy in flight
+}
+
+template <int S, int R, bool DRAG>
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
+    k_pass2_collide_tma(const mlbi_params p, const float *__restrict__ dg, const mlbi_entry *__restrict__ tab,
+                        const float4 *__restrict__ pst, float *__restrict__ fout, unsigned int *__restrict__ flags,
+                        const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_mom,
+                        const __grid_constant__ CUtensorMap map_rest)
+{
+    pass2_collide_tma_tile<S, R, DRAG>(p, dg, tab, pst, fout, flags, &map_f, &map_mom, &map_rest, blockIdx.x,
+                                       blockIdx.y, blockIdx.z);
+}
+
+// every member of a group (block table entries {member, bx, by, bz}); odd:
+// the members read f[cur ^ 1] and write f[cur]
+template <int S, int R, bool DRAG>
+__global__ void __launch_bounds__(kBX * kBY, S <= 2 ? 4 : 2)
+    k_pass2_collide_group(const mlbi_member *__restrict__ mem, const int4 *__restrict__ blk, int odd)
+{
+    __shared__ mlbi_params sp;
+    const int4 e = blk[blockIdx.x];
+    const mlbi_member *m = mem + e.x;
+    const int rd = m->cur ^ odd;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        tensormap_acquire(&m->map_f[rd]);
+        tensormap_acquire(&m->map_mom);
+        tensormap_acquire(&m->map_frest);
+    }
+    group_params(m, sp);
+    const mlbi_buffers &b = m->b;
+    pass2_collide_tma_tile<S, R, DRAG>(sp, b.dg, b.table, b.pst, b.f[rd ^ 1], b.flags, &m->map_f[rd], &m->map_mom,
+                                       &m->map_frest, e.y, e.z, e.w);
 }
 
 template <int S, int R, bool DRAG>
@@ -605,7 +640,60 @@ cudaError_t launch_pass2_collide(const mlbi_params &p, const mlbi_buffers &b, in
     return cudaErrorInvalidValue;          // the global-memory pass 2 is not fused
 }
 
+template <int S, int R, bool DRAG>
+cudaError_t launch_pass2_collide_group(const mlbi_group &g, int odd, cudaStream_t s)
+{
+    using G = TmaTile<S, R>;
+    if constexpr (G::bytes + sizeof(mlbi_params) > kMaxSharedPerBlock) {
+        return cudaErrorInvalidValue;
+    } else {
+        auto k = k_pass2_collide_group<S, R, DRAG>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::bytes);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)g.nblk[MLBI_GROUP_PASS2], dim3(kBX, kBY), G::bytes, s>>>(g.mem, g.blk[MLBI_GROUP_PASS2], odd);
+        return cudaGetLastError();
+    }
+}
+
+template <int S, int R>
+cudaError_t launch_pass2_collide_group_r(const mlbi_group &g, int odd, cudaStream_t s)
+{
+    return g.drag ? launch_pass2_collide_group<S, R, true>(g, odd, s)
+                  : launch_pass2_collide_group<S, R, false>(g, odd, s);
+}
+
 }  // namespace
+
+cudaError_t mlbi_launch_group_pass2_collide(const mlbi_group &g, int odd, cudaStream_t s)
+{
+    if (g.nblk[MLBI_GROUP_PASS2] < 1) return cudaErrorInvalidValue;
+    if (g.S == 1) return g.R == 1 ? launch_pass2_collide_group_r<1, 1>(g, odd, s)
+                                  : launch_pass2_collide_group_r<1, 2>(g, odd, s);
+    if (g.S == 2) return g.R == 1 ? launch_pass2_collide_group_r<2, 1>(g, odd, s)
+                                  : launch_pass2_collide_group_r<2, 2>(g, odd, s);
+    return cudaErrorInvalidValue;
+}
+
+bool mlbi_group_supported(const mlbi_params &p, const mlbi_buffers &b)
+{
+    if (p.S < 1 || p.S > 2 || !p.local_g || p.hc_from_attr || !b.maps || !b.maps->ok) return false;
+    if (p.tile_r != 1 && p.tile_r != 2) return false;
+    return mlbi_pass2_collide_supported(p);
+}
+
+void mlbi_group_grid(const mlbi_params &p, int stage, int grid[3])
+{
+    const int zc = (p.nz + p.zchunk - 1) / p.zchunk;
+    if (stage == MLBI_GROUP_MOMENTS) {
+        grid[0] = (int)grid_for(p.N);
+        grid[1] = grid[2] = 1;
+    } else {
+        const int ty = stage == MLBI_GROUP_PASS1 ? mlbi_tile_ty(p.S, p.tile_r) : kBY;
+        grid[0] = (p.nx + kBX - 1) / kBX;
+        grid[1] = (p.ny + ty - 1) / ty;
+        grid[2] = zc;
+    }
+}
 
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s)
 {

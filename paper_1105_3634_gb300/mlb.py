@@ -107,6 +107,10 @@ def _load():
     L.mlb_batch_step.restype = st
     L.mlb_batch_synchronize.argtypes = [vp]
     L.mlb_batch_synchronize.restype = st
+    L.mlb_batch_set_grouping.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
+    L.mlb_batch_set_grouping.restype = st
+    L.mlb_batch_grouped_members.argtypes = [vp]
+    L.mlb_batch_grouped_members.restype = ctypes.c_int32
     L.mlb_batch_last_error.argtypes = [vp]
     L.mlb_batch_last_error.restype = ctypes.c_char_p
     L.mlb_batch_destroy.argtypes = [vp]
@@ -371,9 +375,11 @@ class Batch:
     """Independent Simulations stepped together through one captured CUDA
     graph (mlb_batch_*).  The members stay usable on their own; they must
     outlive the batch.  stream: a torch.cuda.Stream (default: one the batch
-    creates)."""
+    creates).  lanes: members of at most max_sites sites that take the same
+    kernels step by one launch per stage and lane, 0 = every member by its
+    own launches (mlb_batch_set_grouping)."""
 
-    def __init__(self, sims, stream=None):
+    def __init__(self, sims, stream=None, lanes: int = 1, max_sites: int = 1 << 17):
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s.ctx.value for s in self.sims])
         self.b = ctypes.c_void_p()
@@ -381,6 +387,12 @@ class Batch:
         st = lib.mlb_batch_create(arr, len(self.sims), sp, ctypes.byref(self.b))
         if st != 0:
             raise MLBError(st, "mlb_batch_create failed")
+        if lanes != 1 or max_sites != 1 << 17:
+            self._check(lib.mlb_batch_set_grouping(self.b, int(lanes), int(max_sites)))
+
+    def grouped_members(self) -> int:
+        """Members stepped by grouped launches in the current capture."""
+        return int(lib.mlb_batch_grouped_members(self.b))
 
     def _check(self, st):
         if st != 0:

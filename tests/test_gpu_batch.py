@@ -128,3 +128,64 @@ def test_batch_rejects_bad_members(gpu):
     batch.close()
     sim.close()
     fresh.close()
+
+
+def grouped_members():
+    """Members for the grouped launches: the benchmark spheres periodic and in
+    a sheared channel, with attractive tails (the FP32 column kernel and the
+    tensor-core mean field), two drag-only members (a second group), and
+    three that step by their own launches: nx not a multiple of 4 (no bulk
+    tensor copies), two predictor sweeps, reach-3 shells."""
+    eps = 0.5 * W.KT_LATTICE
+    tails = dict(eps=[[eps] * 2 for _ in range(2)], lambda_c=[[2.5] * 2 for _ in range(2)])
+    sig = [1.0, 1.5]
+    n0 = W.densities_from_packing(0.2, sig, [0.5, 0.5])
+    out = []
+    lat = W.Lattice(shape=(32, 16, 12), sigma=sig)
+    out.append((lat, W.sine_wave(lat, n0, 0.05)))
+    lat = W.Lattice(shape=(40, 12, 16), sigma=sig, wall_axis=1, wall_u_lo=(-0.03, 0.0, 0.0),
+                    wall_u_hi=(0.03, 0.0, 0.0))
+    out.append((lat, W.noise(lat, n0, 0.02, seed=3)))
+    lat = W.Lattice(shape=(24, 16, 16), sigma=sig, **tails)
+    out.append((lat, W.noise(lat, n0, 0.02, seed=5)))
+    lat = W.Lattice(shape=(36, 20, 16), sigma=sig, meanfield="bf16", **tails)
+    out.append((lat, W.noise(lat, n0, 0.02, seed=6)))
+    for shape, seed in (((28, 12, 8), 7), ((20, 8, 8), 8)):
+        lat = W.Lattice(shape=shape, sigma=sig, drag_only=True)
+        out.append((lat, W.noise(lat, n0, 0.02, seed=seed)))
+    lat = W.Lattice(shape=(18, 12, 8), sigma=sig)
+    out.append((lat, W.noise(lat, n0, 0.02, seed=9)))
+    lat = W.Lattice(shape=(24, 12, 8), sigma=sig)
+    lat.predictor_sweeps = 2
+    out.append((lat, W.noise(lat, n0, 0.02, seed=10)))
+    out.append(W.binary_attraction((18, 16, 16), seed=4))
+    return out
+
+
+@pytest.mark.parametrize("nsteps", [6, 9])
+def test_grouped_launches_equal_members_alone(gpu, nsteps):
+    """Six members step by grouped launches (two groups: with and without the
+    drag-only flag; in one lane per group, in two lanes, or not grouped),
+    three by their own; every member's populations equal those of
+    the member stepped alone bit for bit."""
+    import torch
+    cases = grouped_members()
+    alone = []
+    for lat, n in cases:
+        sim = make(gpu, torch, lat, n)
+        sim.step(nsteps)
+        alone.append(sim.populations()[0])
+        sim.close()
+    for lanes in (1, 2, 0):
+        sims = [make(gpu, torch, lat, n) for lat, n in cases]
+        batch = gpu.Batch(sims, lanes=lanes)
+        batch.step(nsteps)
+        batch.synchronize()
+        assert batch.grouped_members() == (6 if lanes else 0)
+        for k, sim in enumerate(sims):
+            f, _, step = sim.populations()
+            assert step == nsteps
+            assert np.array_equal(f.view(np.uint32), alone[k].view(np.uint32)), (lanes, k)
+        batch.close()
+        for sim in sims:
+            sim.close()
