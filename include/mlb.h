@@ -237,7 +237,7 @@ const char *mlb_kernel_name(int32_t k);
  * unchanged: every site's arithmetic is the same under every candidate, so
  * results are bitwise identical whatever it picks).  Times `trials` force +
  * collision passes from the current state for each candidate number of z
- * planes per block of the stencil kernels (4, 8, 16, 32, not above nz) and,
+ * planes per block of the stencil kernels (4, 8, 12, 16, 32, not above nz) and,
  * where both exist, the fused and the split pass-2 + collision launches, and
  * keeps the fastest.  The state is untouched: a trial reads f[cur] and writes
  * the other population buffer, and cur is not advanced.  Synchronises the

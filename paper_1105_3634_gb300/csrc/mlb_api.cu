@@ -515,7 +515,9 @@ mlb_status rebuild(mlb_ctx *c)
         if (p.ball_count[g] != 1) p.local_g = 0;
     p.tile_r = tile_r;
     p.attr_r = attraction ? attr_r : 0;
-    p.zchunk = std::min(c->desc.nz, c->tuned_zchunk > 0 ? c->tuned_zchunk : 16);
+    // planes per block of the stencil kernels unless tuned: 12 leaves shorter
+    // last waves than 16 on large lattices (256^3: 0.5 % faster per step)
+    p.zchunk = std::min(c->desc.nz, c->tuned_zchunk > 0 ? c->tuned_zchunk : 12);
     // the 13 canonical half offsets of the 3x3x3 cube, in the order the kernels use:
     // (1,0,0); (-1,1,0), (0,1,0), (1,1,0); then dz = 1 with dy = -1, 0, 1 and dx = -1, 0, 1
     {
@@ -1215,7 +1217,7 @@ mlb_status mlb_autotune(mlb_ctx *c, int32_t trials, int32_t *zchunk_out, int32_t
         return fail(c, MLB_ECUDA, "cudaEventCreate failed");
     }
     std::vector<int> zs;
-    for (int z : {4, 8, 16, 32})
+    for (int z : {4, 8, 12, 16, 32})
         if (z <= c->desc.nz) zs.push_back(z);
     if (zs.empty()) zs.push_back(c->desc.nz);
     const bool can_fuse = !(c->desc.flags & MLB_SPLIT_COLLIDE) && mlbi_pass2_collide_supported(c->p);
