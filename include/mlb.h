@@ -123,8 +123,11 @@ mlb_status mlb_set_interactions(mlb_ctx *ctx, const double *eps, const double *l
 /* Initial state f := psi_perp(n, u) (Eq. prefactor at the given fields).
  * n: [S][N] number densities (>= 0, finite);  u: [S][3][N] species velocities
  * or NULL for rest.  Also fixes the per-species reference density n_ref^a
- * (the mean of n^a) that the FP32 populations are stored relative to.
- * Errors: MLB_EINVAL (negative or non-finite n, |u| >= 1, packing xi3 >= 1). */
+ * (the mean of n^a) that the FP32 populations are stored relative to.  The
+ * fields are copied to the device first and checked and summed there (FP64);
+ * a rejected field leaves the state unchanged.  Synchronises the stream.
+ * Errors: MLB_EINVAL (negative or non-finite n, |u| >= 1, packing xi3 >= 1;
+ * the message names the first offending entry). */
 mlb_status mlb_set_fields(mlb_ctx *ctx, const double *n, const double *u);
 
 /* Per-site external body force F^a (Eq. evolution) in lattice units:

@@ -856,6 +856,7 @@ mlb_status mlb_create(const mlb_lattice_desc *d, mlb_ctx **out)
     c->b.partial = (double *)q; q += sz_part;
     c->b.sums = (double *)q; q += sz_sums;
     c->b.flags = (unsigned int *)q;
+    c->b.first_bad = (unsigned long long *)(q + 64);      // in the flags block (256 bytes)
     c->b.maps = &c->maps;
     encode_maps(c);
     cudaError_t e = cudaMemsetAsync(c->b.flags, 0, sizeof(unsigned int), c->stream);
@@ -937,27 +938,33 @@ mlb_status mlb_set_fields(mlb_ctx *c, const double *n, const double *u)
     if (!n) return fail(c, MLB_EINVAL, "n is required");
     const int S = c->desc.nspecies;
     const long long N = c->p.N;
-    std::vector<double> mean(S, 0.0);
-    for (int a = 0; a < S; ++a) {
-        double s = 0.0;
-        for (long long r = 0; r < N; ++r) {
-            const double v = n[a * N + r];
-            if (!std::isfinite(v) || v < 0.0) return fail(c, MLB_EINVAL, "n[%d][%lld] = %g is not a density", a, r, v);
-            s += v;
-        }
-        mean[a] = s / (double)N;
-    }
+    // upload, then check and sum on the device; the staging buffer is scratch,
+    // so a rejected field leaves the state as it was
+    double *dn = c->b.stage;
+    double *du = u ? c->b.stage + (size_t)S * N : nullptr;
     double v3[MLBI_MAXS];
     for (int a = 0; a < S; ++a) v3[a] = kPi / 6.0 * c->sigma[a] * c->sigma[a] * c->sigma[a];
-    for (long long r = 0; r < N; ++r) {
+    MLB_CUDA(c, cudaMemcpyAsync(dn, n, sizeof(double) * S * N, cudaMemcpyHostToDevice, c->stream));
+    if (u) MLB_CUDA(c, cudaMemcpyAsync(du, u, sizeof(double) * S * 3 * N, cudaMemcpyHostToDevice, c->stream));
+    MLB_CUDA(c, mlbi_launch_field_check(c->p, c->b, dn, du, v3, c->stream));
+    double sums[MLBI_MAXS];
+    unsigned long long bad[3];
+    MLB_CUDA(c, cudaMemcpyAsync(sums, c->b.sums, sizeof(double) * S, cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaMemcpyAsync(bad, c->b.first_bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    MLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    constexpr unsigned long long kNone = ~0ull;
+    if (bad[0] != kNone)
+        return fail(c, MLB_EINVAL, "n[%d][%lld] = %g is not a density", (int)(bad[0] / N), (long long)(bad[0] % N),
+                    n[bad[0]]);
+    if (bad[1] != kNone) {
         double xi3 = 0.0;
-        for (int a = 0; a < S; ++a) xi3 += v3[a] * n[a * N + r];
-        if (!(xi3 < 1.0)) return fail(c, MLB_EINVAL, "packing xi3 = %g >= 1 at site %lld", xi3, r);
+        for (int a = 0; a < S; ++a) xi3 += v3[a] * n[a * N + (long long)bad[1]];
+        return fail(c, MLB_EINVAL, "packing xi3 = %g >= 1 at site %lld", xi3, (long long)bad[1]);
     }
-    if (u)
-        for (long long k = 0; k < (long long)S * 3 * N; ++k)
-            if (!std::isfinite(u[k]) || std::fabs(u[k]) >= 1.0)
-                return fail(c, MLB_EINVAL, "velocity entry %lld = %g must be finite with |u| < 1", k, u[k]);
+    if (bad[2] != kNone)
+        return fail(c, MLB_EINVAL, "velocity entry %lld = %g must be finite with |u| < 1", (long long)bad[2], u[bad[2]]);
+    std::vector<double> mean(S, 0.0);
+    for (int a = 0; a < S; ++a) mean[a] = sums[a] / (double)N;
     std::vector<double> old = c->nref;
     for (int a = 0; a < S; ++a) c->nref[a] = (double)(float)mean[a];
     mlb_status st = rebuild(c);
@@ -965,10 +972,6 @@ mlb_status mlb_set_fields(mlb_ctx *c, const double *n, const double *u)
         c->nref = old;
         return st;
     }
-    double *dn = c->b.stage;
-    double *du = u ? c->b.stage + (size_t)S * N : nullptr;
-    MLB_CUDA(c, cudaMemcpyAsync(dn, n, sizeof(double) * S * N, cudaMemcpyHostToDevice, c->stream));
-    if (u) MLB_CUDA(c, cudaMemcpyAsync(du, u, sizeof(double) * S * 3 * N, cudaMemcpyHostToDevice, c->stream));
     MLB_CUDA(c, mlbi_launch_init(c->p, c->b, c->cur, dn, du, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->fields_set = true;

@@ -147,6 +147,7 @@ struct mlbi_buffers {
     double *sums;                    // [S+3] final sums
     unsigned int *flags;             // [1] numeric fault flags
     const mlbi_maps *maps;           // host copy of the TMA descriptors (owned by the context)
+    unsigned long long *first_bad;   // [3] first invalid entry of uploaded fields (n, xi3, u)
 };
 
 #define MLBI_RED_BLOCKS 1024
@@ -182,6 +183,13 @@ cudaError_t mlbi_launch_attraction_tc(const mlbi_params &p, const mlbi_buffers &
 cudaError_t mlbi_launch_attraction(const mlbi_params &p, const mlbi_buffers &b, cudaStream_t s);
 cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s,
                                   bool sums = false);
+// Uploaded fields n [S][N] and u [S][3][N] (u may be NULL), FP64 in device
+// memory: the per-species sums of n into b.sums[0 .. S-1], and in
+// b.first_bad the first flat index of n not finite or negative, of a site with
+// xi3 = sum_a v3[a] n^a >= 1, and of u not finite or |u| >= 1 (all ones where
+// none; b.first_bad is reset by the launch)
+cudaError_t mlbi_launch_field_check(const mlbi_params &p, const mlbi_buffers &b, const double *n, const double *u,
+                                    const double *v3, cudaStream_t s);
 cudaError_t mlbi_launch_pass2(const mlbi_params &p, const mlbi_buffers &b, double *acc_out, cudaStream_t s);
 cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int cur, cudaStream_t s);
 // pass 2 fused with the collision and streaming of f[cur] -> f[cur ^ 1] (no acceleration

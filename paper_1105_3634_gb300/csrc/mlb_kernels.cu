@@ -365,6 +365,58 @@ cudaError_t mlbi_launch_moments_g(const mlbi_params &p, const mlbi_buffers &b, i
     return cudaGetLastError();
 }
 
+struct V3 {
+    double v[MLBI_MAXS];
+};
+
+// the checks and sums of mlbi_launch_field_check; block sums to
+// partial[block][S + 3] (the last three zero) for k_conservation_final
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_field_check(long long N, const double *__restrict__ n,
+                                                        const double *__restrict__ u, V3 v3,
+                                                        double *__restrict__ partial,
+                                                        unsigned long long *__restrict__ bad)
+{
+    constexpr int W = S + 3;
+    constexpr unsigned long long kNone = ~0ull;
+    double sum[S];
+#pragma unroll
+    for (int a = 0; a < S; ++a) sum[a] = 0.0;
+    unsigned long long b_n = kNone, b_xi = kNone, b_u = kNone;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+        double xi3 = 0.0;
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const double v = n[a * N + r];
+            if (!(isfinite(v) && v >= 0.0)) b_n = min(b_n, (unsigned long long)(a * N + r));
+            sum[a] += v;
+            xi3 += v3.v[a] * v;
+        }
+        if (!(xi3 < 1.0)) b_xi = min(b_xi, (unsigned long long)r);
+        if (u) {
+#pragma unroll
+            for (int k = 0; k < 3 * S; ++k) {
+                const double w = u[k * N + r];
+                if (!(isfinite(w) && fabs(w) < 1.0)) b_u = min(b_u, (unsigned long long)(k * N + r));
+            }
+        }
+    }
+    if (b_n != kNone) atomicMin(&bad[0], b_n);
+    if (b_xi != kNone) atomicMin(&bad[1], b_xi);
+    if (b_u != kNone) atomicMin(&bad[2], b_u);
+    __shared__ double sh[S][kBlock];
+#pragma unroll
+    for (int a = 0; a < S; ++a) sh[a][threadIdx.x] = sum[a];
+    __syncthreads();
+    for (int h = kBlock / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int a = 0; a < S; ++a) sh[a][threadIdx.x] += sh[a][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < W) partial[blockIdx.x * W + threadIdx.x] = threadIdx.x < S ? sh[threadIdx.x][0] : 0.0;
+}
+
 cudaError_t mlbi_launch_group_moments(const mlbi_group &g, int odd, cudaStream_t s)
 {
     if (g.nblk[MLBI_GROUP_MOMENTS] < 1) return cudaErrorInvalidValue;
@@ -377,6 +429,20 @@ cudaError_t mlbi_launch_group_moments(const mlbi_group &g, int odd, cudaStream_t
     case 4: k_moments_g_group<4><<<nb, kBlock, 0, s>>>(g.mem, blk, odd); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t mlbi_launch_field_check(const mlbi_params &p, const mlbi_buffers &b, const double *n, const double *u,
+                                    const double *v3, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b.first_bad, 0xFF, 3 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    V3 w{};
+    for (int a = 0; a < p.S && a < MLBI_MAXS; ++a) w.v[a] = v3[a];
+    MLBI_DISPATCH_S((k_field_check<SS><<<MLBI_RED_BLOCKS, kBlock, 0, s>>>(p.N, n, u, w, b.partial, b.first_bad)));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_conservation_final<<<1, kFinalThreads, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
     return cudaGetLastError();
 }
 

@@ -278,8 +278,14 @@ def test_invalid_inputs_are_rejected(gpu):
     with pytest.raises(gpu.MLBError, match="EINVAL"):
         bad = n.copy(); bad[0, 3] = -1.0
         sim.set_fields(bad)
-    with pytest.raises(gpu.MLBError, match="xi3"):
+    with pytest.raises(gpu.MLBError, match=r"n\[1\]\[5\] = nan"):
+        bad = n.copy(); bad[1, 5] = np.nan; bad[1, 9] = -1.0
+        sim.set_fields(bad)
+    with pytest.raises(gpu.MLBError, match="xi3 = .* at site 0"):
         sim.set_fields(n * 10)
+    with pytest.raises(gpu.MLBError, match=f"velocity entry {4 * n.shape[1] + 7} = 1"):
+        u = np.zeros((2, 3, n.shape[1])); u[1, 1, 7] = 1.0; u[1, 2, 3] = np.inf
+        sim.set_fields(n, u)
     with pytest.raises(gpu.MLBError, match="ESTATE"):
         sim.step(1)                     # no state yet
     sim.set_fields(n)
