@@ -177,6 +177,30 @@ def taylor_channel(shape=(512, 64, 64), U: float = 0.05) -> Tuple[Lattice, np.nd
     return lat, n
 
 
+def ensemble_attraction(count: int = 64, seed: int = 1106, meanfield: str = "bf16") -> List[Tuple[Lattice, np.ndarray]]:
+    """Independent binary systems with the attractive tails of the attraction
+    workload (sigma = (2, 3), -eps (sigma_ab / r)^6 cut at 2.5 sigma_ab, eps =
+    kT/2; the mean field on the tensor cores by default): cubes of side L in
+    {32, 40, ..., 128}, packing 0.05 .. 0.30 (equal mole fractions, tau = 1),
+    a 5% concentration wave along x, shear U in 0 .. 0.05 as in ensemble()."""
+    r = uniform01(seed, 3 * count).reshape(count, 3)
+    eps = 0.5 * KT_LATTICE
+    tails = dict(eps=[[eps] * 2 for _ in range(2)], lambda_c=[[2.5] * 2 for _ in range(2)])
+    out = []
+    for k in range(count):
+        L = 32 + 8 * int(r[k, 0] * 13)
+        packing = 0.05 + 0.25 * r[k, 1]
+        U = 0.05 * r[k, 2]
+        if U > 0.005:
+            lat = Lattice(shape=(L, L, L), sigma=[2.0, 3.0], wall_axis=1, wall_u_lo=(-U, 0.0, 0.0),
+                          wall_u_hi=(U, 0.0, 0.0), meanfield=meanfield, **tails)
+        else:
+            lat = Lattice(shape=(L, L, L), sigma=[2.0, 3.0], meanfield=meanfield, **tails)
+        n0 = densities_from_packing(packing, lat.sigma, [0.5, 0.5])
+        out.append((lat, sine_wave(lat, n0, 0.05)))
+    return out
+
+
 def ensemble(count: int = 64, seed: int = 1105) -> List[Tuple[Lattice, np.ndarray]]:
     """Independent binary systems of uneven sizes for batched runs: cubes of
     side L in {32, 40, ..., 128}, packing 0.05 .. 0.20 (equal mole fractions,
