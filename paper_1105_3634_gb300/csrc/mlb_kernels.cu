@@ -442,7 +442,10 @@ cudaError_t mlbi_launch_field_check(const mlbi_params &p, const mlbi_buffers &b,
     MLBI_DISPATCH_S((k_field_check<SS><<<MLBI_RED_BLOCKS, kBlock, 0, s>>>(p.N, n, u, w, b.partial, b.first_bad)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_conservation_final<<<1, kFinalThreads, 0, s>>>(p, b.partial, MLBI_RED_BLOCKS, b.sums);
+    // the partials are sums of n itself: no N n_ref term to add
+    mlbi_params q = p;
+    for (int a = 0; a < MLBI_MAXS; ++a) q.nref[a] = 0.f;
+    k_conservation_final<<<1, kFinalThreads, 0, s>>>(q, b.partial, MLBI_RED_BLOCKS, b.sums);
     return cudaGetLastError();
 }
 

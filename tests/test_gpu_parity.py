@@ -270,6 +270,14 @@ def test_zero_steps_and_rerun_determinism(gpu):
     b.set_fields(n)
     b.step(7)
     assert np.array_equal(a.populations()[0].view(np.uint32), b.populations()[0].view(np.uint32))
+    # fields set again on a used context: the same reference densities and state
+    a.set_fields(n)
+    c = gpu.Simulation(lat)
+    c.set_fields(n)
+    fa, nref_a, _ = a.populations()
+    fc, nref_c, _ = c.populations()
+    assert np.array_equal(nref_a, nref_c)
+    assert np.array_equal(fa.view(np.uint32), fc.view(np.uint32))
 
 
 def test_invalid_inputs_are_rejected(gpu):
