@@ -699,6 +699,53 @@ def run_variants(mlb, torch, plain_value, plain_ms):
     batch.close()
     for sim in sims:
         sim.close()
+    # many small systems (256 x 16^3): the batch (grouped launches, one graph)
+    # against the same members stepped through mlb_step one after the other
+    # (every call asynchronous on the member's own stream, one wait at the end)
+    small = []
+    for k in range(256):
+        sig = [1.0, 1.5]
+        if k % 2:
+            lat_k = W.Lattice(shape=(16, 16, 16), sigma=sig, wall_axis=1, wall_u_lo=(-0.02, 0.0, 0.0),
+                              wall_u_hi=(0.02, 0.0, 0.0))
+        else:
+            lat_k = W.Lattice(shape=(16, 16, 16), sigma=sig)
+        n0 = W.densities_from_packing(0.05 + 0.15 * (k % 7) / 6, sig, [0.5, 0.5])
+        small.append((lat_k, W.sine_wave(lat_k, n0, 0.05)))
+    ssims = [mlb.Simulation(l, stream=torch.cuda.Stream()) for l, _ in small]
+    for sim, (_, nn) in zip(ssims, small):
+        sim.set_fields(nn)
+    sunits = sum(l.nspecies * l.nsites for l, _ in small)
+    for sim in ssims:
+        sim.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sim in ssims:
+        sim.step(10)
+    torch.cuda.synchronize()
+    ms_turn = (time.perf_counter() - t0) * 1e3 / 10
+    sb = mlb.Batch(ssims, stream=bstream)
+    sb.step(2)
+    sb.synchronize()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(bstream)
+    sb.step(10)
+    e1.record(bstream)
+    sb.synchronize()
+    ms_sb_wall = (time.perf_counter() - t0) * 1e3 / 10
+    ms_sb = e0.elapsed_time(e1) / 10
+    sgrouped = sb.grouped_members()
+    sb.close()
+    for sim in ssims:
+        sim.close()
+    out["ensemble_256_small"] = {
+        "ms_per_ensemble_step": ms_sb, "ms_per_ensemble_step_wall": ms_sb_wall, "value": sunits / ms_sb / 1e3,
+        "ms_per_ensemble_step_members_in_turn": ms_turn, "speedup_vs_members_in_turn": ms_turn / ms_sb_wall,
+        "grouped_members": sgrouped, "species_sites": sunits, "D_mutual_rel_error": 0.0,
+        "config": "256 binary systems 16^3 sigma=(1,1.5), packing 0.05-0.20, half sheared (walls at -+0.02); "
+                  "members in turn: mlb_step(10) per member (asynchronous, own streams), one wait; "
+                  "both timed by the host clock"}
     # the ensemble with attractive tails (sigma 2/3, packing to 0.30): the mean
     # field in FP32 and on the tensor cores
     ens = {}
