@@ -280,22 +280,6 @@ mlb_status build_tc_tables(mlb_ctx *c)
     c->tc.nrows = (int)row_start.size() - 1;
     c->tc.pass3 = (c->desc.flags & MLB_MEANFIELD_BF16_1PASS) ? 0 : 1;
     // tensor maps of the padded copies: dims (z, b, xp, yp), box (8 planes, 1, 144 sites, 1)
-    c->tc.maps_ok = 0;
-    {
-        EncodeTiledFn fn = encode_tiled();
-        if (!fn) return fail(c, MLB_EINVAL, "the BF16 mean field needs cuTensorMapEncodeTiled from the driver");
-        const cuuint64_t dims[4] = {(cuuint64_t)p.nz, (cuuint64_t)S, (cuuint64_t)nxp, (cuuint64_t)nyp};
-        const cuuint64_t strides[3] = {(cuuint64_t)p.nz * 2, (cuuint64_t)S * p.nz * 2, (cuuint64_t)nxp * S * p.nz * 2};
-        const cuuint32_t box[4] = {8, 1, 144, 1}, ones[4] = {1, 1, 1, 1};
-        void *srcs[2] = {c->tc.qhi, c->tc.qlo};
-        CUtensorMap *maps[2] = {&c->tc.map_hi, &c->tc.map_lo};
-        for (int k = 0; k < 2; ++k)
-            if (fn(maps[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, srcs[k], dims, strides, box, ones,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return fail(c, MLB_EINVAL, "could not encode the tensor maps of the BF16 density copies");
-        c->tc.maps_ok = 1;
-    }
     MLB_CUDA(c, cudaMemcpyAsync(c->tc.weights, w.data(), w.size() * 2, cudaMemcpyHostToDevice, c->stream));
     MLB_CUDA(c, cudaMemcpyAsync(c->tc.cols, cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice,
                                 c->stream));

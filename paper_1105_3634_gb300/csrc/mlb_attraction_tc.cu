@@ -20,16 +20,16 @@
 // single-product form A_hi B_hi is a flag).
 //
 // The densities are first copied (k_attraction_prep) into BF16 hi and lo
-// arrays [yp][xp][b][z] padded by 8 sites on both sides in x and y (the
-// periodic images, or -n_ref beyond a wall) and in x up to whole tiles, so
-// one row's chunk (b, 8 planes) for the 144 staged sites is a single
-// in-bounds bulk tensor copy.
+// arrays [yp][b][z / 8][xp][8 planes] padded by 8 sites on both sides in x
+// and y (the periodic images, or -n_ref beyond a wall) and in x up to whole
+// tiles, so one row's chunk (b, 8 planes) for the 144 staged sites is 2304
+// contiguous bytes in exactly the staged layout: one in-bounds bulk copy.
 //
 // Warp roles (one CTA per SM, persistent over tiles):
 //   warp 0      bulk-copies the columns' B into a ring of kStages slots
 //   warp 1      issues the MMAs of a column once its B and its row's A are in,
 //               commits them to the slot's and the row's "empty" barriers
-//   warp 2      copies the A rows (2 S 4 tensor copies per row, hi and lo)
+//   warp 2      copies the A rows (2 S 4 bulk copies per row, hi and lo)
 //   warps 3-6   after every dy row, read that row's accumulator and add it to
 //               the tile's sums in registers (FP32, round to nearest), then
 //               store G after the tile's last row
@@ -139,10 +139,48 @@ __device__ __forceinline__ void tile_of(const TcArgs &g, long long t, int &x0, i
     z0 = (int)(r / g.ny % nzt) * kTZ;
 }
 
+// Tensor-memory reads of the epilogue: 32 (or 16) consecutive accumulator
+// columns of the warp's 32 lanes into v, without waiting; tmem_wait waits
+// for the thread's loads and only then lets v's registers be read (the empty
+// asm statements order every later use of v after the wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) asm volatile("" : "+r"(v[i]));
+}
+template <int W, int NS>
+__device__ __forceinline__ void add_chunk(float (&sum)[NS], int c0, const uint32_t (&v)[32])
+{
+#pragma unroll
+    for (int i = 0; i < W; ++i) sum[c0 + i] += __uint_as_float(v[i]);
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_attraction_tc(const TcArgs g, const __grid_constant__ CUtensorMap map_hi,
-                    const __grid_constant__ CUtensorMap map_lo, const uint4 *__restrict__ wts,
+    k_attraction_tc(const TcArgs g, const uint4 *__restrict__ qhi, const uint4 *__restrict__ qlo,
+                    const uint4 *__restrict__ wts,
                     const int2 *__restrict__ cols, const int *__restrict__ row_start, float4 *__restrict__ attr,
                     unsigned int *__restrict__ flags)
 {
@@ -264,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp == 2) {
-        // ---- A producer: per row, 2 S 4 tensor copies of [144 sites][8 planes]
+        // ---- A producer: per row, 2 S 4 bulk copies of [144 sites][8 planes]
         if (lane == 0) {
             const uint32_t row_bytes = (g.pass3 ? 2u : 1u) * Sh::a_bytes;
             const int nzc = g.nz / 8;
@@ -283,8 +321,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             int zc = (z0 - 8) / 8 + j;                  // z0 is a multiple of 16, nz of 8
                             zc = ((zc % nzc) + nzc) % nzc;
                             const uint32_t dst = a_hi + (uint32_t)((b * (kWin / 8) + j) * kXW) * 16;
-                            tma_load_4d(dst, &map_hi, a_full + 8 * as, 8 * zc, b, x0, yp);
-                            if (g.pass3) tma_load_4d(dst + Sh::a_bytes, &map_lo, a_full + 8 * as, 8 * zc, b, x0, yp);
+                            const size_t e0 = (((size_t)yp * S + b) * nzc + zc) * g.nxp + x0;
+                            bulk_load(dst, qhi + e0, kXW * 16, a_full + 8 * as);
+                            if (g.pass3) bulk_load(dst + Sh::a_bytes, qlo + e0, kXW * 16, a_full + 8 * as);
                         }
                 }
             }
@@ -311,18 +350,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t taddr = tmem + buf * kAccCols + lanes;
-#pragma unroll
-                for (int q = 0; q < S * 3; ++q) {
-                    uint32_t v[16];
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                                 "%10, %11, %12, %13, %14, %15}, [%16];"
-                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                                 : "r"(taddr + (uint32_t)(q * kTZ)));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int z = 0; z < kTZ; ++z) sum[q * kTZ + z] += __uint_as_float(v[z]);
+                // the row's 48 S columns in chunks of 32, the next chunk's load
+                // in flight while the current one is added
+                uint32_t va[32], vb[32];
+                tmem_ld32(taddr, va);
+                tmem_wait(va);
+                if constexpr (S == 2) {
+                    tmem_ld32(taddr + 32, vb);
+                    add_chunk<32>(sum, 0, va);
+                    tmem_wait(vb);
+                    tmem_ld32(taddr + 64, va);
+                    add_chunk<32>(sum, 32, vb);
+                    tmem_wait(va);
+                    add_chunk<32>(sum, 64, va);
+                } else {
+                    tmem_ld16(taddr + 32, vb);
+                    add_chunk<32>(sum, 0, va);
+                    tmem_wait(vb);
+                    add_chunk<16>(sum, 32, vb);
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(d_empty + 8 * buf);
@@ -352,9 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // n - n_ref of every species as BF16 hi + lo (hi = RN(v), lo = RN(v - hi)) in
-// the padded z-innermost layout [yp][xp][b][z] the tensor copies read: site
+// the padded layout [yp][b][z / 8][xp][8 planes] the bulk copies read: site
 // (xp - 8, yp - 8) wrapped periodically, or -n_ref beyond a wall; one thread
-// per (xp, yp, b) and 8 planes
+// per (xp, 8 planes, b, yp), consecutive threads at consecutive xp
 __global__ void __launch_bounds__(256) k_attraction_prep(const mlbi_params p, int nxp, int nyp,
                                                          const float4 *__restrict__ mom, uint4 *__restrict__ qhi,
                                                          uint4 *__restrict__ qlo)
@@ -363,11 +408,11 @@ __global__ void __launch_bounds__(256) k_attraction_prep(const mlbi_params p, in
     const long long total = (long long)nxp * nyp * p.S * nzc;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int zc = (int)(e % nzc);
-        long long rest = e / nzc;
-        const int b = (int)(rest % p.S);
-        rest /= p.S;
-        const int xp = (int)(rest % nxp), yp = (int)(rest / nxp);
+        const int xp = (int)(e % nxp);
+        long long rest = e / nxp;
+        const int zc = (int)(rest % nzc);
+        rest /= nzc;
+        const int b = (int)(rest % p.S), yp = (int)(rest / p.S);
         const int xg = xp - kPad, yg = yp - kPad;
         const bool out = (p.wall_axis == 0 && (xg < 0 || xg >= p.nx)) || (p.wall_axis == 1 && (yg < 0 || yg >= p.ny));
         const int x = ((xg % p.nx) + p.nx) % p.nx, y = ((yg % p.ny) + p.ny) % p.ny;
@@ -413,7 +458,7 @@ size_t mlbi_attraction_tc_column_bytes(int S)
 cudaError_t mlbi_launch_attraction_tc(const mlbi_params &p, const mlbi_buffers &b, const mlbi_tc_tables &t,
                                       cudaStream_t s)
 {
-    if (!mlbi_attraction_tc_supported(p) || !t.weights || !t.qhi || !t.qlo || !t.maps_ok) return cudaErrorInvalidValue;
+    if (!mlbi_attraction_tc_supported(p) || !t.weights || !t.qhi || !t.qlo) return cudaErrorInvalidValue;
     TcArgs g{};
     g.nx = p.nx; g.ny = p.ny; g.nz = p.nz; g.S = p.S; g.wall_axis = p.wall_axis; g.N = p.N;
     mlbi_attraction_tc_padded(p, &g.nxp, &g.nyp);
@@ -435,13 +480,13 @@ cudaError_t mlbi_launch_attraction_tc(const mlbi_params &p, const mlbi_buffers &
         auto k = k_attraction_tc<1>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape<1>::smem);
         if (e != cudaSuccess) return e;
-        k<<<grid, kThreads, Shape<1>::smem, s>>>(g, t.map_hi, t.map_lo, (const uint4 *)t.weights, t.cols,
+        k<<<grid, kThreads, Shape<1>::smem, s>>>(g, (const uint4 *)t.qhi, (const uint4 *)t.qlo, (const uint4 *)t.weights, t.cols,
                                                  t.row_start, b.attr, b.flags);
     } else {
         auto k = k_attraction_tc<2>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape<2>::smem);
         if (e != cudaSuccess) return e;
-        k<<<grid, kThreads, Shape<2>::smem, s>>>(g, t.map_hi, t.map_lo, (const uint4 *)t.weights, t.cols,
+        k<<<grid, kThreads, Shape<2>::smem, s>>>(g, (const uint4 *)t.qhi, (const uint4 *)t.qlo, (const uint4 *)t.weights, t.cols,
                                                  t.row_start, b.attr, b.flags);
     }
     return cudaGetLastError();

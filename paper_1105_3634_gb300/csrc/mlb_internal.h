@@ -119,14 +119,12 @@ struct mlbi_maps {
 // Tables of the tensor-core attraction (mlb_attraction_tc.cu), device memory
 // owned by the context: per column (dx, dy), sorted by dy then dx, the B
 // operands hi and lo; the columns and the first column of every dy row; the
-// BF16 hi / lo copies of n - n_ref in the layout [y][x][b][z].
+// BF16 hi / lo copies of n - n_ref in the layout [y][b][z / 8][x][8 planes].
 struct mlbi_tc_tables {
     void *weights;                   // [ncols][hi, lo][K / 8][N][8] BF16
     int2 *cols;                      // [ncols] (dx, dy)
     int *row_start;                  // [nrows + 1]
-    void *qhi, *qlo;                 // [nyp][nxp][S][nz] BF16 each (padded, mlbi_attraction_tc_padded)
-    CUtensorMap map_hi, map_lo;      // 4D tensor maps of qhi / qlo: (z, b, xp, yp), box (8, 1, 144, 1)
-    int maps_ok;
+    void *qhi, *qlo;                 // [nyp][S][nz / 8][nxp][8] BF16 each (padded, mlbi_attraction_tc_padded)
     int ncols, nrows;
     int pass3;                       // 1: compensated hi/lo product, 0: hi only
 };
