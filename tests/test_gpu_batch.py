@@ -133,8 +133,8 @@ def test_batch_rejects_bad_members(gpu):
 def grouped_members():
     """Members for the grouped launches: the benchmark spheres periodic and in
     a sheared channel, with attractive tails (the FP32 column kernel and the
-    tensor-core mean field), two drag-only members (a second group), and
-    three that step by their own launches: nx not a multiple of 4 (no bulk
+    tensor-core mean field), walls normal to z and to x, two drag-only
+    members (a second group), and three that step by their own launches: nx not a multiple of 4 (no bulk
     tensor copies), two predictor sweeps, reach-3 shells."""
     eps = 0.5 * W.KT_LATTICE
     tails = dict(eps=[[eps] * 2 for _ in range(2)], lambda_c=[[2.5] * 2 for _ in range(2)])
@@ -153,6 +153,12 @@ def grouped_members():
     for shape, seed in (((28, 12, 8), 7), ((20, 8, 8), 8)):
         lat = W.Lattice(shape=shape, sigma=sig, drag_only=True)
         out.append((lat, W.noise(lat, n0, 0.02, seed=seed)))
+    lat = W.Lattice(shape=(24, 12, 10), sigma=sig, wall_axis=2, wall_u_lo=(0.0, -0.02, 0.0),
+                    wall_u_hi=(0.02, 0.0, 0.0))
+    out.append((lat, W.noise(lat, n0, 0.02, seed=11)))
+    lat = W.Lattice(shape=(20, 12, 12), sigma=sig, wall_axis=0, wall_u_lo=(0.0, 0.0, 0.01),
+                    wall_u_hi=(0.0, -0.01, 0.0))
+    out.append((lat, W.noise(lat, n0, 0.02, seed=12)))
     lat = W.Lattice(shape=(18, 12, 8), sigma=sig)
     out.append((lat, W.noise(lat, n0, 0.02, seed=9)))
     lat = W.Lattice(shape=(24, 12, 8), sigma=sig)
@@ -164,7 +170,7 @@ def grouped_members():
 
 @pytest.mark.parametrize("nsteps", [6, 9])
 def test_grouped_launches_equal_members_alone(gpu, nsteps):
-    """Six members step by grouped launches (two groups: with and without the
+    """Eight members step by grouped launches (two groups: with and without the
     drag-only flag; in one lane per group, in two lanes, or not grouped),
     three by their own; every member's populations equal those of
     the member stepped alone bit for bit."""
@@ -181,7 +187,7 @@ def test_grouped_launches_equal_members_alone(gpu, nsteps):
         batch = gpu.Batch(sims, lanes=lanes)
         batch.step(nsteps)
         batch.synchronize()
-        assert batch.grouped_members() == (6 if lanes else 0)
+        assert batch.grouped_members() == (8 if lanes else 0)
         for k, sim in enumerate(sims):
             f, _, step = sim.populations()
             assert step == nsteps
