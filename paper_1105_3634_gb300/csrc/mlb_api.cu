@@ -545,15 +545,21 @@ mlb_status rebuild(mlb_ctx *c)
     return MLB_OK;
 }
 
+// the status the fault-flag word fl stands for
+mlb_status flags_status(mlb_ctx *c, unsigned int fl)
+{
+    if (fl & MLBI_FLAG_TIMEOUT) return fail(c, MLB_ETIMEOUT, "a bounded wait on a bulk tensor copy gave up");
+    if (fl & MLBI_FLAG_NAN) return fail(c, MLB_ENUMERIC, "non-finite moments met (the state diverged)");
+    if (fl & MLBI_FLAG_XI3) return fail(c, MLB_ENUMERIC, "packing fraction xi3 >= 1 met at some site");
+    return MLB_OK;
+}
+
 mlb_status check_flags(mlb_ctx *c)
 {
     unsigned int fl = 0;
     MLB_CUDA(c, cudaMemcpyAsync(&fl, c->b.flags, sizeof fl, cudaMemcpyDeviceToHost, c->stream));
     MLB_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (fl & MLBI_FLAG_TIMEOUT) return fail(c, MLB_ETIMEOUT, "a bounded wait on a bulk tensor copy gave up");
-    if (fl & MLBI_FLAG_NAN) return fail(c, MLB_ENUMERIC, "non-finite moments met (the state diverged)");
-    if (fl & MLBI_FLAG_XI3) return fail(c, MLB_ENUMERIC, "packing fraction xi3 >= 1 met at some site");
-    return MLB_OK;
+    return flags_status(c, fl);
 }
 
 mlb_status require_ready(mlb_ctx *c)
@@ -1348,6 +1354,10 @@ struct mlb_batch {
     void *gmem = nullptr;                     // device: member tables and block tables of every lane
     std::vector<cudaEvent_t> lane_ev;         // per lane: lane done
     cudaEvent_t attr_fork = nullptr;
+    // mlb_batch_synchronize: every member's flag word gathered by one kernel
+    const unsigned int **flag_ptrs = nullptr;  // device [n]
+    unsigned int *flag_words = nullptr;         // device [n]
+    unsigned int *flag_host = nullptr;          // pinned host [n]
     bool failed = false;
     std::string err;
 };
@@ -1614,6 +1624,14 @@ mlb_status mlb_batch_create(mlb_ctx *const *members, int32_t n, void *stream, ml
         e = cudaEventCreateWithFlags(&b->cap_done[i], fl);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->pre[i], fl);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&b->flag_ptrs, sizeof(unsigned int *) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->flag_words, sizeof(unsigned int) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->flag_host, sizeof(unsigned int) * n);
+    if (e == cudaSuccess) {
+        std::vector<const unsigned int *> ptrs(n);
+        for (int32_t i = 0; i < n; ++i) ptrs[i] = members[i]->b.flags;
+        e = cudaMemcpy(b->flag_ptrs, ptrs.data(), sizeof(unsigned int *) * n, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         mlb_batch_destroy(b);
         return MLB_ECUDA;
@@ -1660,15 +1678,27 @@ mlb_status mlb_batch_step(mlb_batch *b, int64_t nsteps)
     return MLB_OK;
 }
 
+// Waits for every member's stream (each joined into the batch stream by an
+// event), then reads all members' fault flags with one gather launch and one
+// copy, and reports the first member whose flags are set.
 mlb_status mlb_batch_synchronize(mlb_batch *b)
 {
     if (!b) return MLB_EINVAL;
     if (b->failed) return MLB_ESTATE;
-    const cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
-    for (size_t i = 0; i < b->m.size(); ++i) {
-        const mlb_status st = mlb_synchronize(b->m[i]);
-        if (st != MLB_OK) return batch_fail(b, st, "member %zu: %s", i, b->m[i]->err.c_str());
+    const int n = (int)b->m.size();
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(b->pre[i], b->m[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->pre[i], 0);
+    }
+    if (e == cudaSuccess) e = mlbi_launch_gather_flags(b->flag_ptrs, n, b->flag_words, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->flag_host, b->flag_words, sizeof(unsigned int) * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, MLB_ECUDA, "synchronize: %s", cudaGetErrorString(e));
+    for (int i = 0; i < n; ++i) {
+        const mlb_status st = flags_status(b->m[i], b->flag_host[i]);
+        if (st != MLB_OK) return batch_fail(b, st, "member %d: %s", i, b->m[i]->err.c_str());
     }
     return MLB_OK;
 }
@@ -1710,6 +1740,9 @@ void mlb_batch_destroy(mlb_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     free_groups(b);
+    if (b->flag_ptrs) cudaFree(b->flag_ptrs);
+    if (b->flag_words) cudaFree(b->flag_words);
+    if (b->flag_host) cudaFreeHost(b->flag_host);
     for (cudaEvent_t e : b->lane_ev)
         if (e) cudaEventDestroy(e);
     if (b->attr_fork) cudaEventDestroy(b->attr_fork);

@@ -230,6 +230,8 @@ enum { MLBI_GROUP_MOMENTS = 0, MLBI_GROUP_PASS1 = 1, MLBI_GROUP_PASS2 = 2 };
 // whether a member can join a group, and its stage grids (blocks per stage)
 bool mlbi_group_supported(const mlbi_params &p, const mlbi_buffers &b);
 void mlbi_group_grid(const mlbi_params &p, int stage, int grid[3]);
+// out[i] = *flags[i] for n contexts' fault-flag words (one launch; mlb_batch)
+cudaError_t mlbi_launch_gather_flags(const unsigned int *const *flags, int n, unsigned int *out, cudaStream_t s);
 // odd: the group's odd step (members read f[cur ^ 1])
 cudaError_t mlbi_launch_group_moments(const mlbi_group &g, int odd, cudaStream_t s);
 cudaError_t mlbi_launch_group_pass1(const mlbi_group &g, cudaStream_t s);

@@ -417,6 +417,20 @@ __global__ void __launch_bounds__(kBlock) k_field_check(long long N, const doubl
     if (threadIdx.x < W) partial[blockIdx.x * W + threadIdx.x] = threadIdx.x < S ? sh[threadIdx.x][0] : 0.0;
 }
 
+__global__ void __launch_bounds__(kBlock) k_gather_flags(const unsigned int *const *__restrict__ flags, int n,
+                                                         unsigned int *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = *flags[i];
+}
+
+cudaError_t mlbi_launch_gather_flags(const unsigned int *const *flags, int n, unsigned int *out, cudaStream_t s)
+{
+    if (n < 1) return cudaErrorInvalidValue;
+    k_gather_flags<<<(n + kBlock - 1) / kBlock, kBlock, 0, s>>>(flags, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t mlbi_launch_group_moments(const mlbi_group &g, int odd, cudaStream_t s)
 {
     if (g.nblk[MLBI_GROUP_MOMENTS] < 1) return cudaErrorInvalidValue;
