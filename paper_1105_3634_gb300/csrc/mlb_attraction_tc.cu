@@ -48,12 +48,15 @@
 namespace {
 
 constexpr int kTM = 128;                 // sites per tile (TMEM lanes)
-constexpr int kTZ = 16;                  // planes per tile
-constexpr int kWin = 32;                 // staged planes z0 - 8 .. z0 + 23
+constexpr int kTZ = 16;                  // planes per sub-tile (one accumulator, N = 48 S)
+constexpr int kSub = 2;                  // z sub-tiles per tile: each column's B serves both
+constexpr int kWin = 32;                 // planes of one sub-tile's window (K = 32 S)
+constexpr int kAwin = kWin + (kSub - 1) * kTZ;   // staged planes z0 - 8 .. z0 + 39
 constexpr int kXW = kTM + 16;            // staged sites x0 - 8 .. x0 + 135
-constexpr int kStages = 6;               // B ring slots (the copies' look-ahead: 6 columns of MMAs)
-constexpr int kThreads = 224;
-constexpr int kEpi = 128;                // warps 3..6
+constexpr int kStages = 4;               // B ring slots (the copies' look-ahead: 4 columns of MMAs)
+constexpr int kEpiWarps = 4 * kSub;      // warps 3 .. 10: a lane quarter of one sub-tile each
+constexpr int kThreads = 96 + 32 * kEpiWarps;
+constexpr int kEpi = 32 * kEpiWarps;
 constexpr int kPad = 8;                  // halo of the padded density copies
 constexpr uint32_t kAccCols = 128;       // columns per accumulator (N <= 96 used)
 constexpr int kMaxCols = 17 * 17;        // columns of a reach-8 region
@@ -73,7 +76,8 @@ struct Shape {
     static constexpr int N = 3 * S * kTZ;                    // outputs per site
     static constexpr int K = kWin * S;                       // (species, plane) values
     static constexpr int KC = K / 8;                         // 16-byte chunks along K
-    static constexpr uint32_t a_bytes = (uint32_t)KC * kXW * 16;            // one staged row, hi or lo
+    static constexpr int AC = kAwin / 8 * S;                 // staged 16-byte chunks of A (kAwin planes)
+    static constexpr uint32_t a_bytes = (uint32_t)AC * kXW * 16;            // one staged row, hi or lo
     static constexpr uint32_t b_bytes = (uint32_t)KC * N * 16;              // one column's B, hi or lo
     static constexpr uint32_t col_bytes = 2 * b_bytes;                      // hi + lo
     // instruction descriptor (kind::f16): D FP32, A and B BF16, both K-major,
@@ -132,30 +136,18 @@ __device__ __forceinline__ void commit(uint32_t bar)
 // tile t -> (x0, y, z0)
 __device__ __forceinline__ void tile_of(const TcArgs &g, long long t, int &x0, int &y, int &z0)
 {
-    const int nxt = (g.nx + kTM - 1) / kTM, nzt = (g.nz + kTZ - 1) / kTZ;
+    const int nxt = (g.nx + kTM - 1) / kTM, nzt = (g.nz + kSub * kTZ - 1) / (kSub * kTZ);
     x0 = (int)(t % nxt) * kTM;
     const long long r = t / nxt;
     y = (int)(r % g.ny);
-    z0 = (int)(r / g.ny % nzt) * kTZ;
+    z0 = (int)(r / g.ny % nzt) * (kSub * kTZ);
 }
 
-// Tensor-memory reads of the epilogue: 32 (or 16) consecutive accumulator
-// columns of the warp's 32 lanes into v, without waiting; tmem_wait waits
-// for the thread's loads and only then lets v's registers be read (the empty
-// asm statements order every later use of v after the wait).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                 "[%32];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[32])
+// Tensor-memory reads of the epilogue: 16 consecutive accumulator columns of
+// the warp's 32 lanes into v, without waiting; tmem_wait waits for the
+// thread's loads and only then lets v's registers be read (the empty asm
+// statements order every later use of v after the wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                  "%13, %14, %15}, [%16];"
@@ -164,17 +156,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[32])
                    "=r"(v[15])
                  : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32])
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[16])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) asm volatile("" : "+r"(v[i]));
+    for (int i = 0; i < 16; ++i) asm volatile("" : "+r"(v[i]));
 }
-template <int W, int NS>
-__device__ __forceinline__ void add_chunk(float (&sum)[NS], int c0, const uint32_t (&v)[32])
+// sum[c] += accumulator column c for the NC columns of one row (chunks of 16,
+// the next chunk's load in flight while the current one is added)
+template <int NC>
+__device__ __forceinline__ void add_row(float (&sum)[NC], uint32_t taddr)
 {
+    constexpr int NCH = NC / 16;
+    uint32_t v[2][16];
+    tmem_ld16(taddr, v[0]);
+    tmem_wait(v[0]);
 #pragma unroll
-    for (int i = 0; i < W; ++i) sum[c0 + i] += __uint_as_float(v[i]);
+    for (int i = 0; i < NCH; ++i) {
+        if (i + 1 < NCH) tmem_ld16(taddr + 16 * (i + 1), v[(i + 1) & 1]);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sum[16 * i + k] += __uint_as_float(v[i & 1][k]);
+        if (i + 1 < NCH) tmem_wait(v[(i + 1) & 1]);
+    }
 }
 
 template <int S>
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(2 * kAccCols)
+                     "r"(2 * kSub * kAccCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    const int nxt = (g.nx + kTM - 1) / kTM, nzt = (g.nz + kTZ - 1) / kTZ;
+    const int nxt = (g.nx + kTM - 1) / kTM, nzt = (g.nz + kSub * kTZ - 1) / (kSub * kTZ);
     const long long ntiles = (long long)nxt * g.ny * nzt;
 
     if (warp == 0) {
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // the row's accumulator: free once the epilogue read it two rows ago
                     if (r >= 2 && !wait_or_abort(d_empty + 8 * buf, ((r / 2) - 1) & 1, abort)) break;
                     if (!wait_or_abort(a_full + 8 * as, (r / 2) & 1, abort)) break;
-                    const uint32_t d = tmem + buf * kAccCols;
+                    const uint32_t d = tmem + buf * kSub * kAccCols;      // sub-tile s at d + s kAccCols
                     uint32_t acc = 0;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a_hi = a_base + as * 2 * Sh::a_bytes, a_lo = a_hi + Sh::a_bytes;
@@ -278,16 +281,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t ah = mdesc(a_hi + (uint32_t)(8 + dx) * 16, kXW * 16, 128);
                         const uint64_t al = mdesc(a_lo + (uint32_t)(8 + dx) * 16, kXW * 16, 128);
                         const uint64_t bh = mdesc(b_hi, Sh::N * 16, 128), bl = mdesc(b_lo, Sh::N * 16, 128);
+                        // K step q: species q / 2, planes 16 (q % 2) .. + 15 of the
+                        // sub-tile's window, which starts 2 s chunks into the staged row
 #pragma unroll
                         for (int q = 0; q < Sh::K / 16; ++q) {
-                            const uint64_t ao = (uint64_t)((q * 2 * kXW * 16) >> 4);
                             const uint64_t bo = (uint64_t)((q * 2 * Sh::N * 16) >> 4);
-                            mma(d, ah + ao, bh + bo, Sh::idesc, acc);
-                            acc = 1;
-                            if (g.pass3) {
-                                mma(d, ah + ao, bl + bo, Sh::idesc, 1);
-                                mma(d, al + ao, bh + bo, Sh::idesc, 1);
+#pragma unroll
+                            for (int sub = 0; sub < kSub; ++sub) {
+                                const int chunk = (q / 2) * (kAwin / 8) + 2 * (q % 2) + 2 * sub;
+                                const uint64_t ao = (uint64_t)((chunk * kXW * 16) >> 4);
+                                const uint32_t ds = d + sub * kAccCols;
+                                mma(ds, ah + ao, bh + bo, Sh::idesc, acc);
+                                if (g.pass3) {
+                                    mma(ds, ah + ao, bl + bo, Sh::idesc, 1);
+                                    mma(ds, al + ao, bh + bo, Sh::idesc, 1);
+                                }
                             }
+                            acc = 1;
                         }
                         commit(b_empty + 8 * s);                     // the slot is free once these finish
                     }
@@ -302,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp == 2) {
-        // ---- A producer: per row, 2 S 4 bulk copies of [144 sites][8 planes]
+        // ---- A producer: per row, 2 S 6 bulk copies of [144 sites][8 planes]
         if (lane == 0) {
             const uint32_t row_bytes = (g.pass3 ? 2u : 1u) * Sh::a_bytes;
             const int nzc = g.nz / 8;
@@ -317,10 +327,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int yp = y + s_dy[row] + kPad;
                     mbar_expect_tx(a_full + 8 * as, row_bytes);
                     for (int b = 0; b < S; ++b)
-                        for (int j = 0; j < kWin / 8; ++j) {
-                            int zc = (z0 - 8) / 8 + j;                  // z0 is a multiple of 16, nz of 8
+                        for (int j = 0; j < kAwin / 8; ++j) {
+                            int zc = (z0 - 8) / 8 + j;                  // z0 is a multiple of 32, nz of 8
                             zc = ((zc % nzc) + nzc) % nzc;
-                            const uint32_t dst = a_hi + (uint32_t)((b * (kWin / 8) + j) * kXW) * 16;
+                            const uint32_t dst = a_hi + (uint32_t)((b * (kAwin / 8) + j) * kXW) * 16;
                             const size_t e0 = (((size_t)yp * S + b) * nzc + zc) * g.nxp + x0;
                             bulk_load(dst, qhi + e0, kXW * 16, a_full + 8 * as);
                             if (g.pass3) bulk_load(dst + Sh::a_bytes, qlo + e0, kXW * 16, a_full + 8 * as);
@@ -332,11 +342,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (uint32_t q = r > 2 ? r - 2 : 0; q < r; ++q) mbar_wait(a_full + 8 * (q & 1), (q / 2) & 1);
         }
     } else {
-        // ---- epilogue (warps 3..6: TMEM lanes 32 (warp % 4) ..); every
-        // decision is warp-uniform (__all_sync), so the .sync.aligned
-        // tensor-memory loads always run with the whole warp
+        // ---- epilogue (warps 3..10: TMEM lanes 32 (warp % 4) .. of sub-tile
+        // (warp - 3) / 4); every decision is warp-uniform (__all_sync), so
+        // the .sync.aligned tensor-memory loads always run with the whole warp
         uint32_t r = 0;
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        const int sub = (warp - 3) / 4;
         bool stop = false;
         for (long long t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
             float sum[S * 3 * kTZ];
@@ -349,32 +360,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t taddr = tmem + buf * kAccCols + lanes;
-                // the row's 48 S columns in chunks of 32, the next chunk's load
-                // in flight while the current one is added
-                uint32_t va[32], vb[32];
-                tmem_ld32(taddr, va);
-                tmem_wait(va);
-                if constexpr (S == 2) {
-                    tmem_ld32(taddr + 32, vb);
-                    add_chunk<32>(sum, 0, va);
-                    tmem_wait(vb);
-                    tmem_ld32(taddr + 64, va);
-                    add_chunk<32>(sum, 32, vb);
-                    tmem_wait(va);
-                    add_chunk<32>(sum, 64, va);
-                } else {
-                    tmem_ld16(taddr + 32, vb);
-                    add_chunk<32>(sum, 0, va);
-                    tmem_wait(vb);
-                    add_chunk<16>(sum, 32, vb);
-                }
+                const uint32_t taddr = tmem + (buf * kSub + sub) * kAccCols + lanes;
+                add_row<S * 3 * kTZ>(sum, taddr);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(d_empty + 8 * buf);
             }
             if (stop) break;
             int x0, y, z0;
             tile_of(g, t, x0, y, z0);
+            z0 += sub * kTZ;
             const int x = x0 + (warp & 3) * 32 + lane;
             if (x < g.nx) {
 #pragma unroll
@@ -392,7 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (*abort && tid == 0) atomicOr(flags, MLBI_FLAG_TIMEOUT);
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAccCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kSub * kAccCols)
+                     : "memory");
     }
 }
 
@@ -470,7 +465,7 @@ cudaError_t mlbi_launch_attraction_tc(const mlbi_params &p, const mlbi_buffers &
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const int nxt = (p.nx + kTM - 1) / kTM, nzt = (p.nz + kTZ - 1) / kTZ;
+    const int nxt = (p.nx + kTM - 1) / kTM, nzt = (p.nz + kSub * kTZ - 1) / (kSub * kTZ);
     const long long ntiles = (long long)nxt * p.ny * nzt;
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
