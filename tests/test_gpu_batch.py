@@ -195,3 +195,25 @@ def test_grouped_launches_equal_members_alone(gpu, nsteps):
         batch.close()
         for sim in sims:
             sim.close()
+
+
+def test_grouping_settings(gpu):
+    """Only members of at most max_sites sites are grouped; bad settings are refused."""
+    import torch
+    cases = grouped_members()[:2]                  # 6144 and 7680 sites, both groupable
+    sims = [make(gpu, torch, lat, n) for lat, n in cases]
+    batch = gpu.Batch(sims, max_sites=7000)        # only the first fits: a group of one is not formed
+    batch.step(2)
+    batch.synchronize()
+    assert batch.grouped_members() == 0
+    batch.close()
+    batch = gpu.Batch(sims, max_sites=8000)
+    batch.step(2)
+    batch.synchronize()
+    assert batch.grouped_members() == 2
+    for bad in ((65, 1 << 17), (-1, 1 << 17), (1, 0)):
+        with pytest.raises(gpu.MLBError, match="lanes|max_sites"):
+            batch._check(gpu.lib.mlb_batch_set_grouping(batch.b, *bad))
+    batch.close()
+    for sim in sims:
+        sim.close()
