@@ -134,7 +134,8 @@ def grouped_members():
     """Members for the grouped launches: the benchmark spheres periodic and in
     a sheared channel, with attractive tails (the FP32 column kernel and the
     tensor-core mean field), walls normal to z and to x, two drag-only
-    members (a second group), and three that step by their own launches: nx not a multiple of 4 (no bulk
+    members (a second group), one species with shells of reach 1 and of
+    reach 2 (two more groups), and three that step by their own launches: nx not a multiple of 4 (no bulk
     tensor copies), two predictor sweeps, reach-3 shells."""
     eps = 0.5 * W.KT_LATTICE
     tails = dict(eps=[[eps] * 2 for _ in range(2)], lambda_c=[[2.5] * 2 for _ in range(2)])
@@ -159,6 +160,10 @@ def grouped_members():
     lat = W.Lattice(shape=(20, 12, 12), sigma=sig, wall_axis=0, wall_u_lo=(0.0, 0.0, 0.01),
                     wall_u_hi=(0.0, -0.01, 0.0))
     out.append((lat, W.noise(lat, n0, 0.02, seed=12)))
+    for sig1, shape, seed in (([1.0], (24, 8, 8), 13), ([1.0], (16, 12, 8), 14),
+                              ([1.75], (24, 12, 12), 15), ([1.75], (32, 8, 12), 16)):
+        lat = W.Lattice(shape=shape, sigma=sig1)
+        out.append((lat, W.noise(lat, W.densities_from_packing(0.2, sig1, [1.0]), 0.03, seed=seed)))
     lat = W.Lattice(shape=(18, 12, 8), sigma=sig)
     out.append((lat, W.noise(lat, n0, 0.02, seed=9)))
     lat = W.Lattice(shape=(24, 12, 8), sigma=sig)
@@ -170,8 +175,9 @@ def grouped_members():
 
 @pytest.mark.parametrize("nsteps", [6, 9])
 def test_grouped_launches_equal_members_alone(gpu, nsteps):
-    """Eight members step by grouped launches (two groups: with and without the
-    drag-only flag; in one lane per group, in two lanes, or not grouped),
+    """Twelve members step by grouped launches (four groups: two species with
+    and without the drag-only flag, one species at reach 1 and 2; in one lane
+    per group, in two lanes, or not grouped),
     three by their own; every member's populations equal those of
     the member stepped alone bit for bit."""
     import torch
@@ -187,7 +193,7 @@ def test_grouped_launches_equal_members_alone(gpu, nsteps):
         batch = gpu.Batch(sims, lanes=lanes)
         batch.step(nsteps)
         batch.synchronize()
-        assert batch.grouped_members() == (8 if lanes else 0)
+        assert batch.grouped_members() == (12 if lanes else 0)
         for k, sim in enumerate(sims):
             f, _, step = sim.populations()
             assert step == nsteps
