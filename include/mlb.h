@@ -366,6 +366,14 @@ mlb_status mlb_surrogate_status(mlb_ctx *ctx, int32_t *active, double *last_erro
  * roofline fractions are quoted against.) */
 mlb_status mlb_copy_bandwidth(int64_t bytes, int32_t reps, double *gbs);
 
+/* FP32 FMA throughput in TFLOP/s (2 flops per FMA): 2048 threads per SM,
+ * each `iters` rounds of 16 independent FMA chains (as packed FP32 pairs),
+ * `reps` >= 1 launches timed with CUDA events after one untimed one, on the
+ * current device.  Errors: MLB_EINVAL, MLB_ENOMEM, MLB_ECUDA.  (No
+ * counterpart in the paper: the arithmetic peak the arithmetic-bound
+ * kernels are quoted against.) */
+mlb_status mlb_fma_throughput(int32_t iters, int32_t reps, double *tflops);
+
 /* Conservation sums without any allocation (the paper has no counterpart:
  * this serves callers that cannot let the library allocate).  A caller whose
  * device memory is all owned by its own memory manager (a framework pool, a

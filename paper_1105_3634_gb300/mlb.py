@@ -99,6 +99,8 @@ def _load():
     L.mlb_step_monitored.restype = st
     L.mlb_copy_bandwidth.argtypes = [ctypes.c_int64, ctypes.c_int32, dp]
     L.mlb_copy_bandwidth.restype = st
+    L.mlb_fma_throughput.argtypes = [ctypes.c_int32, ctypes.c_int32, dp]
+    L.mlb_fma_throughput.restype = st
     L.mlb_autotune.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     L.mlb_autotune.restype = st
     L.mlb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
@@ -159,6 +161,16 @@ def _dp(a):
         return None
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def fma_throughput(iters: int = 1 << 14, reps: int = 10) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s
+    (mlb_fma_throughput)."""
+    out = ctypes.c_double()
+    rc = lib.mlb_fma_throughput(int(iters), int(reps), ctypes.byref(out))
+    if rc != 0:
+        raise MLBError(rc, "mlb_fma_throughput failed")
+    return out.value
 
 
 def copy_bandwidth(nbytes: int = 1 << 31, reps: int = 20) -> float:

@@ -470,3 +470,15 @@ def test_predictor_sweeps_match_the_oracle(gpu, orc, case, sweeps):
     w = run_pair(gpu, orc, lat, n, u, checkpoints=cps, report=rep)
     print(case, sweeps, rep)
     assert ok(w), w
+
+
+def test_measured_peaks_are_plausible(gpu):
+    """The project's peak probes: the FP32 FMA kernel reaches most of the
+    nominal rate (152 SMs x 128 lanes x 2 flops at up to 2.07 GHz = 80.5
+    TFLOP/s), and the copy kernel most of the HBM3e bandwidth."""
+    tf = gpu.fma_throughput(1 << 12, 3)
+    assert 40.0 < tf < 82.0, tf
+    gbs = gpu.copy_bandwidth(1 << 30, 3)
+    assert 3000.0 < gbs < 8500.0, gbs
+    with pytest.raises(gpu.MLBError):
+        gpu.fma_throughput(0, 1)
