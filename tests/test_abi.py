@@ -88,7 +88,7 @@ def test_null_arguments(mlbmod):
 
 def test_new_entry_points_validate_before_touching_the_gpu(mlbmod):
     """Host-side argument checks of the surrogate network, the monitored step
-    and the copy-bandwidth probe: refused with MLB_EINVAL, no device call."""
+    and the copy-bandwidth and FMA probes: refused with MLB_EINVAL, no device call."""
     L = mlbmod.lib
     assert L.mlb_net_param_count() == 27 * 32 * 2 + 32 + 27 * 32 * 32 + 32 + 6 * 32 + 6
     net = ctypes.c_void_p()
@@ -99,6 +99,9 @@ def test_new_entry_points_validate_before_touching_the_gpu(mlbmod):
     assert L.mlb_copy_bandwidth(1 << 19, 5, ctypes.byref(out)) == 1          # below 1 MiB
     assert L.mlb_copy_bandwidth(1 << 24, 0, ctypes.byref(out)) == 1          # no repetition
     assert L.mlb_copy_bandwidth(1 << 24, 5, None) == 1
+    assert L.mlb_fma_throughput(0, 5, ctypes.byref(out)) == 1                 # no iteration
+    assert L.mlb_fma_throughput(64, 0, ctypes.byref(out)) == 1                # no repetition
+    assert L.mlb_fma_throughput(64, 5, None) == 1
     sums = np.zeros(8)
     assert L.mlb_step_monitored(None, sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
     assert L.mlb_attach_surrogate(None, None, 50, 0.05) == 1
