@@ -446,6 +446,7 @@ def test_monitored_steps_report_the_conservation_sums(gpu):
     ("attraction", 3),           # sigma = 2/3 with tails: reach-3 tiles, the column attraction kernel
     ("drag_walls", 2),           # drag only (partner u* at the site), reach-2 tiles, walls normal to z
     ("reach4", 2),               # the global-memory passes
+    ("channel3", 2),             # three species between moving walls (sigma 2, 2.5, 3; contact-value balls)
 ])
 def test_predictor_sweeps_match_the_oracle(gpu, orc, case, sweeps):
     """Further Jacobi sweeps of the half step on the GPU against the oracle
@@ -461,6 +462,10 @@ def test_predictor_sweeps_match_the_oracle(gpu, orc, case, sweeps):
                         wall_u_lo=(-0.02, 0.0, 0.0), wall_u_hi=(0.02, 0.0, 0.0))
         n = W.noise(lat, W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5]), 0.03, seed=7)
         u, cps = W.random_velocities(lat, 0.01, seed=5), (0, 1, 40)
+    elif case == "channel3":
+        lat, n = W.taylor_channel((40, 16, 10), U=0.05)
+        n[2] = n[2] * 1e3 / 8
+        u, cps = None, (0, 1, 40)
     else:
         lat = W.Lattice(shape=(20, 16, 14), sigma=[4.0, 3.0], tau=0.9)
         n = W.noise(lat, W.densities_from_packing(0.2, lat.sigma, [0.5, 0.5]), 0.02, seed=41)
