@@ -202,6 +202,8 @@ __global__ void __launch_bounds__(kBX * kBY, 6) k_collide(const mlbi_params p, c
 }
 
 // ------------------------------------------------------------------ initial populations
+// (one FP64 reciprocal per site: FP64 division is slow on this part)
+template <int S>
 __global__ void __launch_bounds__(kBlock) k_init(mlbi_params p, const double *__restrict__ nin,
                                                  const double *__restrict__ uin, float *__restrict__ f)
 {
@@ -209,16 +211,21 @@ __global__ void __launch_bounds__(kBlock) k_init(mlbi_params p, const double *__
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
          r += (long long)gridDim.x * blockDim.x) {
         double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < p.S; ++a) {
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
             double na = nin[a * N + r];
             rho += na;
             if (uin)
+#pragma unroll
                 for (int q = 0; q < 3; ++q) m[q] += na * uin[(a * 3 + q) * N + r];
         }
+        const double irho = rho > 0.0 ? 1.0 / rho : 0.0;
         float ub[3];
-        for (int q = 0; q < 3; ++q) ub[q] = rho > 0.0 ? (float)(m[q] / rho) : 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ub[q] = (float)(m[q] * irho);
         const float ubub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-        for (int a = 0; a < p.S; ++a) {
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
             const double nad = nin[a * N + r];
             const float na = (float)nad;
             const float dna = (float)(nad - (double)p.nref[a]);
@@ -473,7 +480,7 @@ cudaError_t mlbi_launch_collide(const mlbi_params &p, const mlbi_buffers &b, int
 cudaError_t mlbi_launch_init(const mlbi_params &p, const mlbi_buffers &b, int cur, const double *n,
                              const double *u, cudaStream_t s)
 {
-    k_init<<<grid_for(p.N), kBlock, 0, s>>>(p, n, u, b.f[cur]);
+    MLBI_DISPATCH_S((k_init<SS><<<grid_for(p.N), kBlock, 0, s>>>(p, n, u, b.f[cur])));
     return cudaGetLastError();
 }
 
