@@ -13,11 +13,12 @@ cudaError_t launch_pass1_tiled(const mlbi_params &p, const mlbi_buffers &b, cuda
     } else {
         using T = Tile<S, R, TY>;
         auto k = k_pass1_tiled<S, R, DRAG, TY, MODE>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+        const size_t bytes = T::bytes + staged_table_bytes<T, R>(p);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + TY - 1) / TY),
                      (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
-        k<<<g, dim3(kBX, TY), T::bytes, s>>>(p, b.mom, b.dg, b.table, b.fext, b.attr, b.mom, b.frest, b.pst);
+        k<<<g, dim3(kBX, TY), bytes, s>>>(p, b.mom, b.dg, b.table, b.fext, b.attr, b.mom, b.frest, b.pst);
         return cudaGetLastError();
     }
 }

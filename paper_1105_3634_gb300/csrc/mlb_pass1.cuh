@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass1(const mlbi_params p, const 
 // ------------------------------------------------------------------ tiled variants
 // Shell sums from the tile with the stencil table (same sums as pass1_shells).
 template <int S, int R, bool DRAG, int TY, bool HC>
-__device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
+__device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const mlbi_entry *tab,
                                                   const float4 *sf, const float *sg, int kz, int cidx,
                                                   const Centre<S> &c, const float (&ub)[S][3], const PairW<S> &w,
                                                   Acc1<S> &A)
@@ -272,8 +272,8 @@ __device__ __forceinline__ void pass1_tile_shells(const mlbi_params &p, const ml
         const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
 #pragma unroll 2
         for (int k = k0; k < k1; ++k) {
-            const float4 e0 = __ldg(&tab[2 * k]);
-            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const float4 e0 = tab[2 * k];                   // global or shared (stage_table)
+            const float4 e1 = tab[2 * k + 1];
             const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
             const int sp = ring(kz + dz, T::NSLOT), sm = ring(kz - dz, T::NSLOT);   // ring slots of the +-d planes
             const float4 vp = sf[sp * S * T::PLANE + b * T::PLANE + cidx + off];
@@ -401,6 +401,8 @@ __device__ __forceinline__ void pass1_tile(const mlbi_params &p, const float4 *_
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active = x < p.nx && y < p.ny;
     const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    const mlbi_entry *stab =
+        stage_table<T, R>(p, tab, reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem) + T::bytes));
     int xy[T::J];
     stage_sites<S, R, TY>(p, x0, y0, xy);
     for (int k = 0; k < 2 * R + 1; ++k)
@@ -431,7 +433,7 @@ __device__ __forceinline__ void pass1_tile(const mlbi_params &p, const float4 *_
         Acc1<S> A;
         A.zero();
         if constexpr (R == 1 && TY == kBY) pass1_cube<S, DRAG, HC>(p, sf, sg, kz, cidx, c, ub, w, A);
-        else pass1_tile_shells<S, R, DRAG, TY, HC>(p, tab, sf, sg, kz, cidx, c, ub, w, A);
+        else pass1_tile_shells<S, R, DRAG, TY, HC>(p, stab, sf, sg, kz, cidx, c, ub, w, A);
         if constexpr (MODE == kSweep) {
             sweep_finish<S>(p, r, c, A, frest, pst);
             continue;

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_pass2(const mlbi_params p, const 
 
 // ------------------------------------------------------------------ tiled variants
 template <int S, int R, bool DRAG, int TY, int NSL = 2 * R + 2>
-__device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const mlbi_entry *__restrict__ tab,
+__device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const mlbi_entry *tab,
                                                   const float4 *sf, const float *sg, int kz, int cidx,
                                                   const PairW<S> &w, const float (&us)[S][3], float (&acc)[S][3])
 {
@@ -139,8 +139,8 @@ __device__ __forceinline__ void pass2_tile_shells(const mlbi_params &p, const ml
         const int k0 = p.ushell_start[b], k1 = k0 + p.ushell_count[b];
 #pragma unroll 2
         for (int k = k0; k < k1; ++k) {
-            const float4 e0 = __ldg(&tab[2 * k]);
-            const float4 e1 = __ldg(&tab[2 * k + 1]);
+            const float4 e0 = tab[2 * k];                   // global or shared (stage_table)
+            const float4 e1 = tab[2 * k + 1];
             const int mask = __float_as_int(e1.y), off = __float_as_int(e1.z), dz = __float_as_int(e1.w);
             const int sp = ring(kz + dz, NSL), sm = ring(kz - dz, NSL);
             const float4 vp = sf[sp * S * T::PLANE + b * T::PLANE + cidx + off];
@@ -240,7 +240,7 @@ __device__ __forceinline__ void pass2_cube(const mlbi_params &p, const float4 *s
 // the shell sums of the acceleration of the site at ring position kz of the
 // tile (centre slot cs), added to acc
 template <int S, int R, bool DRAG, int TY, int NSL = 2 * R + 2>
-__device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *__restrict__ tab, const float4 *sf,
+__device__ __forceinline__ void pass2_site(const mlbi_params &p, const mlbi_entry *tab, const float4 *sf,
                                            const float *sg, int kz, int cidx, float (&acc)[S][3])
 {
     using T = Tile<S, R, TY>;
@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active = x < p.nx && y < p.ny;
     const int cidx = (threadIdx.y + R) * T::TXH + threadIdx.x + R;
+    const mlbi_entry *stab =
+        stage_table<T, R>(p, tab, reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem) + T::bytes));
     int xy[T::J];
     stage_sites<S, R, TY>(p, x0, y0, xy);
     for (int k = 0; k < 2 * R + 1; ++k)
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kBX * TY, tile_blocks(Tile<S, R, TY>::bytes, S
         const long long r = x + (long long)p.nx * (y + (long long)p.ny * z);
         float acc[S][3];
         zero_acc<S>(acc);
-        pass2_site<S, R, DRAG, TY>(p, tab, sf, sg, kz, cidx, acc);
+        pass2_site<S, R, DRAG, TY>(p, stab, sf, sg, kz, cidx, acc);
 #pragma unroll
         for (int a = 0; a < S; ++a) add_rest(acc[a], frest[a * p.N + r]);
         store_acc<S>(p, r, acc, acc_f, acc_out);
@@ -573,11 +575,12 @@ cudaError_t launch_pass2_tiled(const mlbi_params &p, const mlbi_buffers &b, doub
     } else {
         using T = Tile<S, R, TY>;
         auto k = k_pass2_tiled<S, R, DRAG, TY>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::bytes);
+        const size_t bytes = T::bytes + staged_table_bytes<T, R>(p);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         const dim3 g((unsigned)((p.nx + kBX - 1) / kBX), (unsigned)((p.ny + TY - 1) / TY),
                      (unsigned)((p.nz + p.zchunk - 1) / p.zchunk));
-        k<<<g, dim3(kBX, TY), T::bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
+        k<<<g, dim3(kBX, TY), bytes, s>>>(p, b.dg, b.table, b.frest, b.pst, b.acc, acc_out);
         return cudaGetLastError();
     }
 }

@@ -135,6 +135,44 @@ struct Tile {
     static_assert(bytes == (size_t)mlbi_tile_bytes(S, R, TY), "tile size formula");
 };
 
+// The shell entries of the table-driven reach-3 tiles, staged once per block
+// into shared memory after the tile: the union shells' range of the table
+// where it fits (one block per SM holds the tile anyway), read there instead
+// of through the L1 on every shell point.  Host and device agree on the size.
+constexpr int kMaxStagedEntries = 512;
+__host__ __device__ inline int shell_entries(const mlbi_params &p, int &lo)
+{
+    lo = p.ushell_start[0];
+    int hi = lo;
+    for (int b = 0; b < p.S; ++b) {
+        lo = p.ushell_start[b] < lo ? p.ushell_start[b] : lo;
+        const int e = p.ushell_start[b] + p.ushell_count[b];
+        hi = e > hi ? e : hi;
+    }
+    return hi - lo;
+}
+template <class T, int R>
+__host__ __device__ inline size_t staged_table_bytes(const mlbi_params &p)
+{
+    if (R != 3) return 0;
+    int lo;
+    const int n = shell_entries(p, lo);
+    const size_t b = (size_t)n * 2 * sizeof(mlbi_entry);
+    return (n <= kMaxStagedEntries && T::bytes + b <= MLBI_MAX_TILE_BYTES) ? b : 0;
+}
+// copy the entries to dst (visible after the caller's next barrier); returns
+// the table the shell loops read
+template <class T, int R>
+__device__ inline const mlbi_entry *stage_table(const mlbi_params &p, const mlbi_entry *tab, float4 *dst)
+{
+    if (staged_table_bytes<T, R>(p) == 0) return tab;
+    int lo;
+    const int n = shell_entries(p, lo);
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int e = tid; e < 2 * n; e += nt) dst[e] = __ldg(&tab[2 * lo + e]);
+    return dst - 2 * lo;
+}
+
 // resident blocks per SM the tile's shared memory allows (at most `cap`)
 constexpr int tile_blocks(size_t bytes, int cap)
 {
