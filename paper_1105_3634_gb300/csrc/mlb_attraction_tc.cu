@@ -6,15 +6,18 @@
 // on sigma_ab <= |d| <= lambda_c sigma_ab (n may be the deviation n - n_ref: K is odd).
 //
 // For one column shift (dx, dy) of the region the sum along z is a band
-// (Toeplitz) matrix product.  A tile is 128 consecutive x sites of one row y
-// and 16 planes z0 .. z0 + 15:
+// (Toeplitz) matrix product.  A sub-tile is 128 consecutive x sites of one
+// row y and 16 planes z0 .. z0 + 15:
 //   D[x][(a, c, z)] += sum_{(b, z')} A_{dx,dy}[x][(b, z')] B_{dx,dy}[(b, z')][(a, c, z)]
 //   A_{dx,dy}[x][(b, z')] = n^b(x + dx, y + dy, z'),   z' = z0 - 8 .. z0 + 23
 //   B_{dx,dy}[(b, z')][(a, c, z)] = K_ab(dx, dy, z' - z)_c   (zero off the region)
-// M = 128 sites, N = 3 S 16 outputs, K = 32 S.  A is staged per row y + dy in a
-// K-major layout [8-value chunk][x'][8 values] holding x' = x0 - 8 .. x0 + 135,
-// so the x shift dx of a column is the same operand with its descriptor start
-// moved by 16 dx bytes.  B (hi and lo) is precomputed per column on the host
+// M = 128 sites, N = 3 S 16 outputs, K = 32 S.  B depends on z' - z only, so
+// a tile holds kSub = 2 sub-tiles (32 planes) whose MMAs share every
+// column's B; the second sub-tile's A is the same staged row 16 planes on.
+// A is staged per row y + dy in a K-major layout [8-value chunk][x'][8 values]
+// holding x' = x0 - 8 .. x0 + 135 and z' = z0 - 8 .. z0 + 39, so the x shift
+// dx of a column is the same operand with its descriptor start moved by 16 dx
+// bytes, and the sub-tile's z shift by two chunks.  B (hi and lo) is precomputed per column on the host
 // (24 KB for S = 2) and streamed from L2 by bulk copies.  The compensated
 // product is A_hi B_hi + A_hi B_lo + A_lo B_hi (three MMAs per K step; the
 // single-product form A_hi B_hi is a flag).
@@ -29,13 +32,15 @@
 //   warp 0      bulk-copies the columns' B into a ring of kStages slots
 //   warp 1      issues the MMAs of a column once its B and its row's A are in,
 //               commits them to the slot's and the row's "empty" barriers
-//   warp 2      copies the A rows (2 S 4 bulk copies per row, hi and lo)
-//   warps 3-6   after every dy row, read that row's accumulator and add it to
-//               the tile's sums in registers (FP32, round to nearest), then
-//               store G after the tile's last row
-// Each dy row has an accumulator of its own (two in tensor memory, used in
-// turn): the tensor pipe's FP32 accumulation then runs over about 140 MMAs
-// instead of the tile's ~2100, and the rows are added on the CUDA cores.
+//   warp 2      copies the A rows (2 S 6 bulk copies per row, hi and lo)
+//   warps 3-10  after every dy row, read that row's accumulator (a lane
+//               quarter of one sub-tile each) and add it to the sub-tile's
+//               sums in registers (FP32, round to nearest), then store G
+//               after the tile's last row
+// Each dy row has an accumulator of its own per sub-tile (two rows in turn:
+// all 512 tensor-memory columns): the tensor pipe's FP32 accumulation then
+// runs over about 140 MMAs instead of the tile's ~2100, and the rows are
+// added on the CUDA cores.
 // Every wait is bounded; one that gives up sets an abort flag every role
 // checks, and the kernel reports it through flags (MLB_ETIMEOUT).
 #include "mlb_internal.h"
