@@ -217,21 +217,24 @@ def dispersion_curve(mlb, lat: W.Lattice, n0: Sequence[float], Us: Sequence[floa
 
 
 # ------------------------------------------------------------------ the paper's experiment (Sec. V, Figs. 3-5)
-def paper_lattice(packing: float, Lx: int, Ly: int = 40, Lz: int = 40, tau: float = 1.0):
+def paper_lattice(packing: float, Lx: int, Ly: int = 40, Lz: int = 40, tau: float = 1.0, sweeps: int = 1):
     """The mixture of Figs. 3-5: sigma_AA = 8, sigma_BB = 4 (contact shells of
     762 points for A-A), equal mole fractions c_0 = 0.5, total packing xi_3
-    (0.211 or 0.332), box L_x x 40 x 40, periodic; tau is not stated (1)."""
+    (0.211 or 0.332), box L_x x 40 x 40, periodic; tau is not stated (1).
+    sweeps: Jacobi sweeps of the half step (1 = the library's default)."""
     lat = W.Lattice(shape=(Lx, Ly, Lz), sigma=[8.0, 4.0], tau=tau)
+    lat.predictor_sweeps = sweeps
     return lat, W.densities_from_packing(packing, lat.sigma, [0.5, 0.5])
 
 
-def paper_curve(mlb, packing: float, Lx: int, pes: Sequence[float], Ly: int = 40, Lz: int = 40) -> Dict:
+def paper_curve(mlb, packing: float, Lx: int, pes: Sequence[float], Ly: int = 40, Lz: int = 40,
+                sweeps: int = 1) -> Dict:
     """Fig. 5: D_eff against Pe = U L_y / (2 D) for the Fig. 3 mixture.  D(0)
     is measured first (no flow), the flow amplitude for each target Pe is
     U = 2 D(0) Pe / L_y, and every fit spans 0.3 to 2.5 decay times of the
     wave; rows give the Pe reached, D_eff / D(0), the exact passive-scalar
     ratio for the flow reached and Eq. taylordiff's 1 + Pe^2 / (2 pi^2)."""
-    lat, n0 = paper_lattice(packing, Lx, Ly, Lz)
+    lat, n0 = paper_lattice(packing, Lx, Ly, Lz, sweeps=sweeps)
     kx = 2.0 * math.pi / Lx
     ky = 2.0 * math.pi / Ly
 
@@ -251,19 +254,20 @@ def paper_curve(mlb, packing: float, Lx: int, pes: Sequence[float], Ly: int = 40
         rows.append({"Pe_target": pe, "U": U, "Pe": pe_r, "D_eff": Deff, "ratio": Deff / D0,
                      "ratio_passive_scalar": passive_scalar_rate(D0, Ur, kx, ky) / D0,
                      "ratio_eq_taylordiff": 1.0 + pe_r * pe_r / (2.0 * math.pi ** 2)})
-    return {"packing": packing, "Lx": Lx, "Ly": Ly, "Lz": Lz, "D0": D0, "nu": nu, "rows": rows}
+    return {"packing": packing, "Lx": Lx, "Ly": Ly, "Lz": Lz, "sweeps": sweeps, "D0": D0, "nu": nu, "rows": rows}
 
 
 if __name__ == "__main__":  # pragma: no cover
-    # python -m paper_1105_3634_gb300.taylor [--packings 0.211 0.332] [--lx 40 80] [--pe 0.5 1 1.5 2]
+    # python -m paper_1105_3634_gb300.taylor [--packings 0.211 0.332] [--lx 40 80] [--pe 0.5 1 1.5 2] [--sweeps 1]
     import argparse
     import json
     ap = argparse.ArgumentParser(description="Taylor dispersion of Sec. V (Figs. 3-5) on the GPU")
     ap.add_argument("--packings", type=float, nargs="+", default=[0.211, 0.332])
     ap.add_argument("--lx", type=int, nargs="+", default=[40, 80])
     ap.add_argument("--pe", type=float, nargs="+", default=[0.5, 1.0, 1.5, 2.0])
+    ap.add_argument("--sweeps", type=int, default=1, help="Jacobi sweeps of the half step (1..8)")
     args = ap.parse_args()
     from . import mlb as _mlb
     for packing in args.packings:
         for Lx in args.lx:
-            print(json.dumps(paper_curve(_mlb, packing, Lx, args.pe)), flush=True)
+            print(json.dumps(paper_curve(_mlb, packing, Lx, args.pe, sweeps=args.sweeps)), flush=True)
